@@ -1,0 +1,206 @@
+/*
+ * gpm.h -- C ABI of libgpm.so: GPU (sm_103a) approximate graph pattern mining
+ * by neighbour sampling with eager verify and online convergence detection,
+ * plus colour sparsification and the hybrid choice between the two.
+ *
+ * Method: "Accurate and Fast Approximate Graph Pattern Mining at Scale"
+ * (ScaleGPM).  Every entry point cites the passage that defines what it
+ * computes.
+ *
+ * Conventions that hold for every call:
+ *  - Return value: GPM_OK (0) or a negative gpm_status.  On error a
+ *    thread-local message is available from gpm_last_error().
+ *  - Outputs are caller-allocated; the library never frees caller memory.
+ *  - A gpm_graph owns its device copy of the graph (or borrows the caller's
+ *    device arrays, see GPM_DEVICE_PTRS) and all device scratch it needs; calls
+ *    on one handle run on the handle's CUDA stream and are not thread-safe for
+ *    the same handle.  Different handles are independent.
+ *  - Vertex ids are uint32; neighbour lists are sorted ascending; the graph is
+ *    symmetric without self loops or duplicate edges (the paper's CSR, Sec. 6).
+ *  - Sample s of a run draws its random words from Philox4x32-10 keyed by the
+ *    run's seed and counted by s, so results do not depend on the launch shape.
+ */
+#ifndef GPM_H
+#define GPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GPM_MAX_K 12          /* size of the per-sample record arrays */
+#define GPM_MAX_PATTERN_K 10  /* largest pattern the planner accepts */
+
+typedef struct gpm_graph gpm_graph;   /* opaque handle */
+
+typedef enum {
+    GPM_OK = 0,
+    GPM_ERR_ARG = -1,             /* bad argument (null pointer, size, pattern) */
+    GPM_ERR_GRAPH = -2,           /* CSR failed validation: unsorted, duplicate, loop, asymmetric, out of range */
+    GPM_ERR_OOM = -3,             /* device allocation failed */
+    GPM_ERR_CUDA = -4,            /* a CUDA runtime call failed */
+    GPM_ERR_NOT_CONVERGED = -5,   /* n_max or max_seconds reached; the result is filled */
+    GPM_ERR_ABORTED = -6,         /* gpm_abort() was called; the result is filled */
+    GPM_ERR_UNSUPPORTED = -8      /* the combination of options is not implemented */
+} gpm_status;
+
+typedef enum {
+    GPM_NS = 0,          /* neighbour sampling with eager verify (Sec. 4.1-4.2) */
+    GPM_GS = 1,          /* colour sparsification + exact count (Sec. 2.2.2, 5.2) */
+    GPM_HYBRID = 2,      /* cost-model choice between NS and GS (Sec. 4.3-4.4, 5.1) */
+    GPM_NS_LEARNED = 3,  /* NS with the learned, importance-weighted proposal */
+    GPM_EXACT = 4        /* exact count on the full graph */
+} gpm_scheme;
+
+typedef enum {
+    GPM_VERIFY_INTERSECT = 0,  /* draw from the full candidate set S_j (Algorithm 4) */
+    GPM_VERIFY_CHECK = 1       /* draw from one restricted list L_j, verify S_j membership by binary search */
+} gpm_verify;
+
+/* gpm_load_csr flags */
+#define GPM_DEVICE_PTRS 1u   /* row_ptr/col are device pointers, borrowed for the handle's lifetime */
+#define GPM_VALIDATE    2u   /* check the CSR invariants on the device (GPM_ERR_GRAPH if violated) */
+
+/* A connected pattern with k vertices; bit j of adj[i] marks the edge i-j
+ * (the matrix must be symmetric without diagonal).  induced = 1 counts
+ * vertex-induced occurrences (motif counting), 0 edge-induced. */
+typedef struct {
+    uint8_t k;
+    uint8_t induced;
+    uint16_t adj[16];
+} gpm_pattern;
+
+/* BF16 weights of the learned proposal's 3 -> 64 -> 64 -> 1 ReLU MLP, as raw
+ * 16-bit patterns, row-major [out][in], in DEVICE memory (4481 values). */
+typedef struct {
+    const uint16_t *w1, *b1, *w2, *b2, *w3, *b3;
+} gpm_mlp;
+
+/* Options; a zeroed struct (or NULL) selects every default. */
+typedef struct {
+    uint64_t window;        /* samples per convergence round W (default 2^20) */
+    uint64_t n_min;         /* no stop before this many samples (default W) */
+    uint64_t n_max;         /* stop unconverged here (default 2^40) */
+    double max_seconds;     /* stop unconverged after this wall time (0 = none) */
+    uint32_t colors;        /* GS colour count c (default 8) */
+    uint32_t slot;          /* pattern slot in the RNG counter (default 0) */
+    uint32_t verify;        /* gpm_verify (default INTERSECT) */
+    uint32_t grid_blocks;   /* sampler launch shape overrides (0 = tuned default) */
+    uint32_t block_warps;
+    uint32_t cap;           /* per-warp on-chip candidate buffer, entries (0 = default) */
+    const gpm_mlp *mlp;     /* GPM_NS_LEARNED: device weights (required) */
+} gpm_config;
+
+typedef struct {
+    double estimate;        /* mu, the estimated count */
+    double ci_half_width;   /* z * sigma (Algorithm 3), z = Phi^-1(1 - delta/2) */
+    double eps_hat;         /* predicted relative error z * sigma / mu (Eq. equ:error) */
+    double sum, sumsq;      /* running sum X_i and sum X_i^2 over all samples */
+    uint64_t samples;       /* n at the stop, a multiple of the window */
+    uint64_t hits;          /* samples with every candidate set non-empty */
+    uint64_t rounds;        /* convergence rounds run */
+    int32_t scheme_used;    /* gpm_scheme that produced the estimate */
+    int32_t converged;      /* 1 if eps_hat <= eps was reached */
+    double t_total_s;       /* wall time of the call */
+    double t_pilot_s;       /* hybrid: pilot NS round and cost models */
+    double t_preproc_s;     /* GS: colouring and sparsification */
+    double t_sample_s;      /* device time of the sampling / counting kernels (CUDA events) */
+    uint64_t exact_count;   /* GS: count on the sparsified graph; EXACT: the count */
+    uint64_t kernel_launches; /* kernels this call launched */
+} gpm_result;
+
+/* One sample's path, for parity checks and training traces. */
+typedef struct {
+    uint64_t factor[GPM_MAX_K]; /* [0] = M (m or 2m), [j] = |S_j| (CHECK: |L_j|; learned: A_j) */
+    uint64_t w_u64;             /* exact weight, 0 on a miss or overflow (learned: 0) */
+    double w_f64;               /* weight as a left-to-right FP64 product, 0 on a miss */
+    uint32_t vert[GPM_MAX_K];   /* matched vertices in matching order, 0xFFFFFFFF past the depth */
+    uint32_t aux[GPM_MAX_K];    /* learned: score a_x of the chosen vertex at step j */
+    uint8_t hit, depth, overflow, pad[5];
+} gpm_sample_record;
+
+/* Totals of a fixed block of samples. */
+typedef struct {
+    uint64_t n, hits;
+    double sum, sumsq;
+} gpm_sums;
+
+/* Load a graph (Sec. 6: symmetric CSR without loops or duplicates).
+ *  n        vertex count (< 2^32 - 1)
+ *  row_ptr  n + 1 offsets into col, row_ptr[0] = 0 (uint64)
+ *  col      row_ptr[n] neighbour ids, each list sorted ascending (uint32)
+ *  flags    GPM_DEVICE_PTRS: both arrays are device pointers the handle borrows
+ *           (the caller keeps them alive and unchanged until gpm_free_graph);
+ *           otherwise they are host arrays that the call copies.
+ *           GPM_VALIDATE: check the invariants on the device.
+ *  stream   cudaStream_t for every call on this handle (NULL = legacy default)
+ *  out      receives the handle
+ * Builds the oriented-edge index (first neighbour above v and the prefix of
+ * upper-degree counts) used to draw the first edge of a sample. */
+gpm_status gpm_load_csr(uint64_t n, const uint64_t *row_ptr, const uint32_t *col, uint32_t flags,
+                        void *stream, gpm_graph **out);
+
+void gpm_free_graph(gpm_graph *g);
+
+/* n, m (undirected edges), 2m, maximum degree. Any output may be NULL. */
+gpm_status gpm_graph_info(const gpm_graph *g, uint64_t *n, uint64_t *m, uint64_t *nnz, uint64_t *max_degree);
+
+/* Estimate the pattern's count to relative error eps with confidence 1-delta.
+ * GPM_NS / GPM_NS_LEARNED: Algorithm 3 over Algorithm 4-style samples, rounds
+ * of cfg->window samples until eps_hat <= eps (Eq. equ:error).
+ * GPM_GS: one colouring with cfg->colors colours, exact count on the
+ * sparsified graph, scaled by c^(k-1) (eps and delta unused, ci = NaN).
+ * GPM_HYBRID: a pilot NS round feeds the cost models of Sec. 4.3-4.4 and the
+ * faster engine runs (Sec. 5.1, loose mode).  GPM_EXACT: exact count.
+ * Returns GPM_ERR_NOT_CONVERGED (result filled) if n_max or max_seconds ends
+ * the run first. */
+gpm_status gpm_estimate(gpm_graph *g, const gpm_pattern *pattern, gpm_scheme scheme, double eps,
+                        double delta, uint64_t seed, const gpm_config *cfg, gpm_result *out);
+
+/* Many (pattern, eps) jobs in one persistent launch per round; job i uses
+ * RNG slot i.  out has count entries. */
+gpm_status gpm_estimate_batch(gpm_graph *g, uint32_t count, const gpm_pattern *patterns,
+                              const double *eps, double delta, uint64_t seed, const gpm_config *cfg,
+                              gpm_result *out);
+
+/* Samples [first, first + count) of an NS run (Algorithm 3's inner loop):
+ * totals of X_i and X_i^2 in FP64.  cfg selects verify mode, slot and MLP. */
+gpm_status gpm_sample_sums(gpm_graph *g, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
+                           uint64_t count, const gpm_config *cfg, gpm_sums *out);
+
+/* Per-sample records of samples [first, first + count) into HOST memory. */
+gpm_status gpm_trace(gpm_graph *g, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
+                     uint64_t count, const gpm_config *cfg, gpm_sample_record *out);
+
+/* Exact count of the pattern (the plan's nested loops over every branch). */
+gpm_status gpm_exact_count(gpm_graph *g, const gpm_pattern *pattern, uint64_t *out);
+
+/* Colour sparsification (Sec. 2.2.2): colour every vertex with
+ * floor(philox_word0 * c / 2^32) and keep monochromatic edges.  Writes the
+ * sparsified CSR into caller-provided DEVICE arrays row_out (n + 1) and
+ * col_out (capacity 2m); *kept receives its entry count. */
+gpm_status gpm_sparsify(gpm_graph *g, uint32_t colors, uint64_t seed, uint32_t colouring, uint32_t slot,
+                        uint64_t *row_out, uint32_t *col_out, uint64_t *kept);
+
+/* Ask a running estimate on this handle to stop at its next round boundary
+ * (it returns GPM_ERR_ABORTED with the partial result). */
+gpm_status gpm_abort(gpm_graph *g);
+
+/* Matching order and symmetry-breaking restrictions of a pattern (for
+ * inspection): order[j] = pattern vertex at position j; restriction r reads
+ * v[res_lo[r]] < v[res_hi[r]]; *oriented = 1 if the first edge is drawn from
+ * the m oriented edges.  Arrays hold GPM_MAX_K and 64 entries. */
+gpm_status gpm_plan(const gpm_pattern *pattern, int32_t *order, int32_t *res_lo, int32_t *res_hi,
+                    int32_t *nres, int32_t *oriented);
+
+/* Phi^-1(p), the standard normal quantile used for z. */
+double gpm_normal_quantile(double p);
+
+const char *gpm_last_error(void);
+const char *gpm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPM_H */

@@ -1,0 +1,129 @@
+"""Thin ctypes binding of libgpm.so (include/gpm.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels.  Importing this module
+does not need a GPU; calling an entry point that touches the device does.
+If libgpm.so is missing the import fails loudly (there is no CPU fallback).
+"""
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libgpm.so")
+
+MAX_K = 12
+
+GPM_OK = 0
+GPM_ERR_ARG = -1
+GPM_ERR_GRAPH = -2
+GPM_ERR_OOM = -3
+GPM_ERR_CUDA = -4
+GPM_ERR_NOT_CONVERGED = -5
+GPM_ERR_ABORTED = -6
+GPM_ERR_UNSUPPORTED = -8
+
+NS, GS, HYBRID, NS_LEARNED, EXACT = 0, 1, 2, 3, 4
+VERIFY_INTERSECT, VERIFY_CHECK = 0, 1
+DEVICE_PTRS, VALIDATE = 1, 2
+
+STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_GRAPH", -3: "ERR_OOM", -4: "ERR_CUDA",
+                -5: "ERR_NOT_CONVERGED", -6: "ERR_ABORTED", -8: "ERR_UNSUPPORTED"}
+
+
+class Pattern(C.Structure):
+    _fields_ = [("k", C.c_uint8), ("induced", C.c_uint8), ("adj", C.c_uint16 * 16)]
+
+
+class MLP(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("w1", "b1", "w2", "b2", "w3", "b3")]
+
+
+class Config(C.Structure):
+    _fields_ = [("window", C.c_uint64), ("n_min", C.c_uint64), ("n_max", C.c_uint64),
+                ("max_seconds", C.c_double), ("colors", C.c_uint32), ("slot", C.c_uint32),
+                ("verify", C.c_uint32), ("grid_blocks", C.c_uint32), ("block_warps", C.c_uint32),
+                ("cap", C.c_uint32), ("mlp", C.POINTER(MLP))]
+
+
+class Result(C.Structure):
+    _fields_ = [("estimate", C.c_double), ("ci_half_width", C.c_double), ("eps_hat", C.c_double),
+                ("sum", C.c_double), ("sumsq", C.c_double), ("samples", C.c_uint64),
+                ("hits", C.c_uint64), ("rounds", C.c_uint64), ("scheme_used", C.c_int32),
+                ("converged", C.c_int32), ("t_total_s", C.c_double), ("t_pilot_s", C.c_double),
+                ("t_preproc_s", C.c_double), ("t_sample_s", C.c_double), ("exact_count", C.c_uint64),
+                ("kernel_launches", C.c_uint64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class SampleRecord(C.Structure):
+    _fields_ = [("factor", C.c_uint64 * MAX_K), ("w_u64", C.c_uint64), ("w_f64", C.c_double),
+                ("vert", C.c_uint32 * MAX_K), ("aux", C.c_uint32 * MAX_K), ("hit", C.c_uint8),
+                ("depth", C.c_uint8), ("overflow", C.c_uint8), ("pad", C.c_uint8 * 5)]
+
+
+class Sums(C.Structure):
+    _fields_ = [("n", C.c_uint64), ("hits", C.c_uint64), ("sum", C.c_double), ("sumsq", C.c_double)]
+
+
+# (name, restype, argtypes): every exported entry point of include/gpm.h
+P = C.POINTER
+_V = C.c_void_p
+_u64, _u32, _i32, _dbl = C.c_uint64, C.c_uint32, C.c_int32, C.c_double
+SIGNATURES = [
+    ("gpm_load_csr", _i32, [_u64, _V, _V, _u32, _V, P(_V)]),
+    ("gpm_free_graph", None, [_V]),
+    ("gpm_graph_info", _i32, [_V, P(_u64), P(_u64), P(_u64), P(_u64)]),
+    ("gpm_estimate", _i32, [_V, P(Pattern), _i32, _dbl, _dbl, _u64, P(Config), P(Result)]),
+    ("gpm_estimate_batch", _i32, [_V, _u32, P(Pattern), P(_dbl), _dbl, _u64, P(Config), P(Result)]),
+    ("gpm_sample_sums", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), P(Sums)]),
+    ("gpm_trace", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), _V]),
+    ("gpm_exact_count", _i32, [_V, P(Pattern), P(_u64)]),
+    ("gpm_sparsify", _i32, [_V, _u32, _u64, _u32, _u32, _V, _V, P(_u64)]),
+    ("gpm_abort", _i32, [_V]),
+    ("gpm_plan", _i32, [P(Pattern), P(_i32), P(_i32), P(_i32), P(_i32), P(_i32)]),
+    ("gpm_normal_quantile", _dbl, [_dbl]),
+    ("gpm_last_error", C.c_char_p, []),
+    ("gpm_version", C.c_char_p, []),
+]
+
+_lib = None
+
+
+def load():
+    """Load libgpm.so (built by ``build.py``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libgpm.so is not built: run python -c 'import __graft_entry__ as g; g.build()'")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        assert C.sizeof(SampleRecord) == 216
+        _lib = L
+    return _lib
+
+
+class GpmError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = load().gpm_last_error().decode(errors="replace")
+        super().__init__("%s failed: %s (%s)" % (where, STATUS_NAMES.get(code, code), msg))
+
+
+def check(code, where, ok=(GPM_OK,)):
+    if code not in ok:
+        raise GpmError(code, where)
+    return code
+
+
+def make_pattern(k, edges, induced=False):
+    p = Pattern()
+    p.k = k
+    p.induced = 1 if induced else 0
+    for a, b in edges:
+        p.adj[a] |= 1 << b
+        p.adj[b] |= 1 << a
+    return p

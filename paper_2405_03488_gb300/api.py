@@ -1,0 +1,167 @@
+"""Python face of libgpm for PyTorch users: graphs held in torch tensors (or
+host numpy arrays), calls on torch's current CUDA stream.  Marshalling only;
+the work runs in libgpm.so."""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from . import graphs as _graphs
+from ._lib import (DEVICE_PTRS, EXACT, GS, HYBRID, NS, NS_LEARNED,  # noqa: F401
+                   VALIDATE, VERIFY_CHECK, VERIFY_INTERSECT, check, make_pattern)
+
+RECORD_DTYPE = np.dtype([("factor", np.uint64, _lib.MAX_K), ("w_u64", np.uint64), ("w_f64", np.float64),
+                         ("vert", np.uint32, _lib.MAX_K), ("aux", np.uint32, _lib.MAX_K), ("hit", np.uint8),
+                         ("depth", np.uint8), ("overflow", np.uint8), ("pad", np.uint8, 5)])
+assert RECORD_DTYPE.itemsize == C.sizeof(_lib.SampleRecord)
+
+
+def pattern(spec, induced=None):
+    """A gpm_pattern from a name ('4-clique', 'house', ...) or (k, edges[, induced])."""
+    if isinstance(spec, _lib.Pattern):
+        return spec
+    if isinstance(spec, str):
+        k, edges = _graphs.pattern(spec)
+        ind = False
+    else:
+        k, edges = spec[0], spec[1]
+        ind = bool(spec[2]) if len(spec) > 2 else False
+    if induced is not None:
+        ind = induced
+    return make_pattern(k, edges, ind)
+
+
+def config(**kw):
+    cfg = _lib.Config()
+    mlp = kw.pop("mlp", None)
+    for key, val in kw.items():
+        if val is None:
+            continue
+        if key == "verify" and isinstance(val, str):
+            val = {"intersect": VERIFY_INTERSECT, "check": VERIFY_CHECK}[val]
+        setattr(cfg, key, val)
+    if mlp is not None:
+        cfg.mlp = C.pointer(mlp.c_struct())
+        cfg._keep = mlp
+    return cfg
+
+
+def _stream_ptr():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Graph:
+    """A resident data graph.
+
+    ``row_ptr`` (int64 / uint64, n + 1) and ``col`` (int32 / uint32, 2m) are
+    either CUDA tensors, which the handle borrows (kept alive here), or host
+    arrays, which the library copies to the device."""
+
+    def __init__(self, row_ptr, col, validate=False):
+        L = _lib.load()
+        self._keep = None
+        flags = VALIDATE if validate else 0
+        h = C.c_void_p()
+        if isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda:
+            row_ptr = row_ptr.contiguous().to(torch.int64)
+            col = col.contiguous().to(torch.int32)
+            self._keep = (row_ptr, col)
+            n = row_ptr.numel() - 1
+            code = L.gpm_load_csr(n, C.c_void_p(row_ptr.data_ptr()), C.c_void_p(col.data_ptr()),
+                                  flags | DEVICE_PTRS, _stream_ptr(), C.byref(h))
+        else:
+            if isinstance(row_ptr, torch.Tensor):
+                row_ptr, col = row_ptr.numpy(), col.numpy()
+            rp = np.ascontiguousarray(row_ptr, dtype=np.uint64)
+            cc = np.ascontiguousarray(col, dtype=np.uint32)
+            n = len(rp) - 1
+            code = L.gpm_load_csr(n, C.c_void_p(rp.ctypes.data), C.c_void_p(cc.ctypes.data if len(cc) else 0),
+                                  flags, _stream_ptr(), C.byref(h))
+        check(code, "gpm_load_csr")
+        self.h = h
+        n_, m_, nnz_, md_ = C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_uint64()
+        check(L.gpm_graph_info(h, C.byref(n_), C.byref(m_), C.byref(nnz_), C.byref(md_)), "gpm_graph_info")
+        self.n, self.m, self.nnz, self.max_degree = n_.value, m_.value, nnz_.value, md_.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.load().gpm_free_graph(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def estimate(self, pat, scheme=NS, eps=0.01, delta=0.01, seed=1, allow_unconverged=True, **cfg):
+        res = _lib.Result()
+        pp = pattern(pat)
+        c = config(**cfg)
+        code = _lib.load().gpm_estimate(self.h, C.byref(pp), scheme, eps, delta, seed, C.byref(c), C.byref(res))
+        ok = (_lib.GPM_OK, _lib.GPM_ERR_NOT_CONVERGED) if allow_unconverged else (_lib.GPM_OK,)
+        check(code, "gpm_estimate", ok)
+        d = res.as_dict()
+        d["status"] = code
+        return d
+
+    def estimate_batch(self, pats, eps, delta=0.01, seed=1, **cfg):
+        L = _lib.load()
+        arr = (_lib.Pattern * len(pats))(*[pattern(p) for p in pats])
+        e = (C.c_double * len(pats))(*eps)
+        res = (_lib.Result * len(pats))()
+        c = config(**cfg)
+        code = L.gpm_estimate_batch(self.h, len(pats), arr, e, delta, seed, C.byref(c), res)
+        check(code, "gpm_estimate_batch", (_lib.GPM_OK, _lib.GPM_ERR_NOT_CONVERGED))
+        return [r.as_dict() for r in res]
+
+    def sample_sums(self, pat, seed, first, count, **cfg):
+        out = _lib.Sums()
+        pp = pattern(pat)
+        c = config(**cfg)
+        check(_lib.load().gpm_sample_sums(self.h, C.byref(pp), seed, first, count, C.byref(c), C.byref(out)),
+              "gpm_sample_sums")
+        return out
+
+    def trace(self, pat, seed, first, count, **cfg):
+        recs = np.zeros(count, dtype=RECORD_DTYPE)
+        pp = pattern(pat)
+        c = config(**cfg)
+        check(_lib.load().gpm_trace(self.h, C.byref(pp), seed, first, count, C.byref(c),
+                                    C.c_void_p(recs.ctypes.data)), "gpm_trace")
+        return recs
+
+    def exact_count(self, pat):
+        out = C.c_uint64()
+        pp = pattern(pat)
+        check(_lib.load().gpm_exact_count(self.h, C.byref(pp), C.byref(out)), "gpm_exact_count")
+        return out.value
+
+    def sparsify(self, colors, seed, colouring=0, slot=0):
+        """Colour sparsification into new CUDA tensors (row_ptr, col)."""
+        row = torch.empty(self.n + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(max(self.nnz, 1), dtype=torch.int32, device="cuda")
+        kept = C.c_uint64()
+        check(_lib.load().gpm_sparsify(self.h, colors, seed, colouring, slot, C.c_void_p(row.data_ptr()),
+                                       C.c_void_p(col.data_ptr()), C.byref(kept)), "gpm_sparsify")
+        return row, col[:kept.value]
+
+    def abort(self):
+        check(_lib.load().gpm_abort(self.h), "gpm_abort")
+
+
+def plan(pat):
+    """(order, restrictions, oriented) from the library's host planner."""
+    pp = pattern(pat)
+    order = (C.c_int32 * _lib.MAX_K)()
+    lo = (C.c_int32 * 64)()
+    hi = (C.c_int32 * 64)()
+    nres = C.c_int32()
+    ori = C.c_int32()
+    check(_lib.load().gpm_plan(C.byref(pp), order, lo, hi, C.byref(nres), C.byref(ori)), "gpm_plan")
+    return list(order[:pp.k]), [(lo[i], hi[i]) for i in range(nres.value)], ori.value
+
+
+def normal_quantile(p):
+    return _lib.load().gpm_normal_quantile(p)

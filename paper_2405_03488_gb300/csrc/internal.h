@@ -1,0 +1,74 @@
+// Internal declarations of libgpm (host and device).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gpm.h"
+
+namespace gpm {
+
+constexpr int kMaxK = GPM_MAX_K;
+
+// Pattern compiled for the sampler: everything is indexed by matching
+// position j (v_0 .. v_{k-1}).
+struct Plan {
+    int32_t k, induced, oriented, nres;
+    int32_t order[kMaxK];         // pattern vertex placed at position j
+    uint32_t back[kMaxK];         // positions i < j adjacent to j in the pattern
+    uint32_t nonback[kMaxK];      // positions i < j not adjacent to j
+    uint32_t lower[kMaxK];        // positions i < j with the restriction v_i < v_j
+    uint32_t reuse[kMaxK];        // 1: S_j = {x in S_{j-1} : x in N(v_{j-1}), x above the bounds}
+    uint32_t last_back[kMaxK];    // largest back-neighbour position of j
+    int32_t res_lo[64], res_hi[64];
+};
+
+// Builds the plan; returns an empty string on success, else the reason.
+std::string build_plan(const gpm_pattern &pat, Plan *out);
+
+// Device view of a resident graph.
+struct DGraph {
+    const uint64_t *row_ptr;   // n + 1
+    const uint32_t *col;       // nnz
+    const uint64_t *up;        // n: index of the first neighbour above v
+    const uint64_t *uoff;      // n + 1: prefix sum of |N+(u)|
+    uint64_t n, nnz, m;
+};
+
+// Per-chunk partial of a sampling round.
+struct Partial {
+    double sum, sumsq;
+    uint64_t hits, n;
+};
+
+// Running totals of a run, updated on the device after each round.
+struct Totals {
+    double sum, sumsq;
+    uint64_t hits, n;
+};
+
+void set_error(const std::string &msg);
+
+}  // namespace gpm
+
+// The opaque handle.
+struct gpm_graph {
+    gpm::DGraph d;
+    cudaStream_t stream;
+    uint64_t max_degree;
+    // owned device memory (null when borrowed)
+    uint64_t *own_row_ptr;
+    uint32_t *own_col;
+    uint64_t *up, *uoff;
+    // sampler scratch
+    gpm::Partial *partials;
+    uint64_t partials_cap;
+    gpm::Totals *totals;          // device
+    gpm::Totals *totals_host;     // pinned
+    unsigned int *counter;        // device chunk counter
+    volatile int abort_flag;
+    int sm_count;
+    cudaEvent_t ev0, ev1;
+};

@@ -1,0 +1,713 @@
+// Neighbour sampling with eager verify (Sec. 4.2, Algorithm 4, Lemma 1) and
+// online convergence detection (Sec. 4.1, Algorithm 3, Eq. equ:error).
+//
+// One warp draws one sample at a time.  Sample s takes its random words from
+// Philox4x32-10 with counter (s_lo, s_hi, block, slot << 8) and key = seed;
+// choice t is the 64-bit word pair (t mod 2) of block t / 2, and an index in
+// [0, N) is floor(r * N / 2^64).
+//
+// Step j of a sample builds the candidate set
+//   S_j = { x : x in N(v_i) for every pattern edge (i, j), i < j;
+//               x not in N(v_i) for every pattern non-edge (i, j) if induced;
+//               x distinct from v_0..v_{j-1}; x > v_a for each restriction a < j }
+// in ascending order, draws x = S_j[floor(r * |S_j| / 2^64)], and multiplies
+// the weight by |S_j|; an empty set ends the sample as a miss (weight 0).
+// The weight starts at M = m (oriented first edge) or 2m.
+//
+// Layout: the warp keeps the partial match, the per-step factors and two
+// candidate buffers of `cap` entries in shared memory; lane i holds the CSR
+// range of v_i.  S_j is built by streaming the shortest back-neighbour list
+// (coalesced 128-byte warp loads) and testing each element against the other
+// lists with per-lane binary searches, compacting survivors with ballots.
+// When S_j extends S_{j-1} by one more adjacency (cliques and similar), it is
+// built from S_{j-1} on chip and only N(v_{j-1}) is read.  A set larger than
+// `cap` is counted in one pass and its drawn element found in a second pass.
+//
+// CHECK mode draws x from the single list L_j = N(v_p) above the lower bound
+// (p the last back-neighbour), weighs |L_j|, and verifies the remaining
+// conditions of S_j with one binary search per lane.
+//
+// Each warp accumulates sum X and sum X^2 (FP64, sample-index order) over a
+// chunk of consecutive samples into a per-chunk partial; chunks are handed out
+// by an atomic counter, and a single-block kernel adds the partials in chunk
+// order, so the result does not depend on scheduling.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace gpm {
+
+enum { MODE_INTERSECT = 0, MODE_CHECK = 1 };
+
+struct RunArgs {
+    uint64_t seed;
+    uint64_t first;               // first sample index of this launch
+    uint64_t count;               // samples in this launch
+    Partial *partials;            // one per chunk
+    unsigned int *counter;        // chunk dispenser
+    gpm_sample_record *trace;     // optional per-sample records (device)
+    uint32_t slot;
+    uint32_t cap;                 // entries per on-chip candidate buffer
+    uint32_t chunk;               // samples per chunk
+    uint32_t nchunks;
+};
+
+constexpr int kWarpHeaderWords = 40;   // 12 u64 factors + 16 u32 vertices
+
+struct WarpMem {
+    uint64_t *fac;
+    uint32_t *v;
+    uint32_t *S0, *S1;
+};
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        uint64_t t = __shfl_xor_sync(kFull, x, o);
+        x = t < x ? t : x;
+    }
+    return x;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+// Conditions of S_j other than membership in the driver list.
+__device__ __forceinline__ bool cand_ok(const DGraph &g, const Plan &p, const uint32_t *v, int j, int driver,
+                                        uint64_t lb, uint64_t le, uint32_t x) {
+    bool ok = true;
+    const uint32_t back = p.back[j];
+    for (int i = 0; i < j; i++) {
+        const uint64_t b = __shfl_sync(kFull, lb, i);
+        const uint64_t e = __shfl_sync(kFull, le, i);
+        ok = ok && (x != v[i]);
+        const bool edge = (back >> i) & 1u;
+        if (edge && i != driver) ok = ok && lane_contains(g.col + b, e - b, x);
+        else if (!edge && p.induced) ok = ok && !lane_contains(g.col + b, e - b, x);
+    }
+    return ok;
+}
+
+// Result of one sample, uniform across the warp.
+struct SampleOut {
+    double w;
+    uint64_t wu;
+    int depth;
+    bool hit, overflow;
+};
+
+template <int MODE>
+__device__ SampleOut sample_one(const DGraph &g, const Plan &p, const RunArgs &a, uint64_t s, WarpMem &wm) {
+    const unsigned lane = lane_id();
+    const int k = p.k;
+    SampleOut out;
+    out.w = 0.0;
+    out.wu = 0;
+    out.depth = 0;
+    out.hit = false;
+    out.overflow = false;
+
+    const int nb = k / 2;  // Philox blocks for the k-1 choices
+    Philox4 o = {0u, 0u, 0u, 0u};
+    if ((int)lane < nb)
+        o = philox10((uint32_t)s, (uint32_t)(s >> 32), lane, a.slot << 8, (uint32_t)a.seed,
+                     (uint32_t)(a.seed >> 32));
+    auto word = [&](int t) -> uint64_t {
+        uint32_t lo = (t & 1) ? o.z : o.x;
+        uint32_t hi = (t & 1) ? o.w : o.y;
+        lo = __shfl_sync(kFull, lo, t >> 1);
+        hi = __shfl_sync(kFull, hi, t >> 1);
+        return ((uint64_t)hi << 32) | lo;
+    };
+
+    const uint64_t M = p.oriented ? g.m : g.nnz;
+    if (lane == 0) wm.fac[0] = M;
+    if (M == 0) return out;
+    const uint64_t e = index_map(word(0), M);
+    uint32_t v0, v1;
+    if (p.oriented) {
+        const uint64_t u = warp_upper_bound(g.uoff, g.n + 1, e) - 1;
+        v0 = (uint32_t)u;
+        v1 = __ldg(g.col + __ldg(g.up + u) + (e - __ldg(g.uoff + u)));
+    } else {
+        const uint64_t u = warp_upper_bound(g.row_ptr, g.n + 1, e) - 1;
+        v0 = (uint32_t)u;
+        v1 = __ldg(g.col + e);
+    }
+    uint64_t lb = 0, le = 0;  // lane i: CSR range of v_i
+    if (lane == 0) {
+        lb = __ldg(g.row_ptr + v0);
+        le = __ldg(g.row_ptr + v0 + 1);
+        wm.v[0] = v0;
+        wm.v[1] = v1;
+    } else if (lane == 1) {
+        lb = __ldg(g.row_ptr + v1);
+        le = __ldg(g.row_ptr + v1 + 1);
+    }
+    __syncwarp();
+    out.depth = 2;
+    double w = (double)M;
+    uint64_t wu = M;
+    bool ovf = false;
+    uint32_t prev_size = 0;
+    bool prev_mat = false;
+
+    for (int j = 2; j < k; j++) {
+        const uint32_t lm = p.lower[j];
+        const bool has_lo = lm != 0;
+        uint32_t lo = 0;
+        for (int i = 0; i < j; i++)
+            if ((lm >> i) & 1u) lo = wm.v[i] > lo ? wm.v[i] : lo;
+        const uint64_t r = word(j - 1);
+        uint64_t size = 0;
+        uint32_t x = 0;
+        if (MODE == MODE_CHECK) {
+            const int pb = (int)p.last_back[j];
+            const uint64_t b = __shfl_sync(kFull, lb, pb);
+            const uint64_t en = __shfl_sync(kFull, le, pb);
+            const uint64_t start = has_lo ? b + warp_upper_bound(g.col + b, en - b, lo) : b;
+            size = en - start;
+            if (lane == 0) wm.fac[j] = size;
+            if (size == 0) {
+                out.depth = j;
+                return out;
+            }
+            x = __ldg(g.col + start + index_map(r, size));
+            bool okl = true;
+            if ((int)lane < j) {
+                okl = (x != wm.v[lane]);
+                const bool edge = (p.back[j] >> lane) & 1u;
+                if (edge) {
+                    if ((int)lane != pb) okl = okl && lane_contains(g.col + lb, le - lb, x);
+                } else if (p.induced) {
+                    okl = okl && !lane_contains(g.col + lb, le - lb, x);
+                }
+            }
+            if (!__all_sync(kFull, okl)) {
+                out.depth = j;
+                return out;
+            }
+        } else {
+            uint32_t *Sc = (j & 1) ? wm.S1 : wm.S0;
+            const uint32_t *Sp = (j & 1) ? wm.S0 : wm.S1;
+            uint64_t count = 0;
+            bool mat;
+            if (p.reuse[j] && prev_mat) {
+                const uint64_t b = __shfl_sync(kFull, lb, j - 1);
+                const uint64_t en = __shfl_sync(kFull, le, j - 1);
+                const uint64_t start = has_lo ? b + warp_upper_bound(g.col + b, en - b, lo) : b;
+                const uint64_t L = en - start;
+                const uint32_t P = prev_size;
+                if (L <= 8ull * P + 32) {
+                    for (uint64_t base = start; base < en; base += 32) {
+                        const uint64_t idx = base + lane;
+                        const bool valid = idx < en;
+                        const uint32_t y = valid ? __ldg(g.col + idx) : 0u;
+                        const bool ok = valid && lane_contains_shared(Sp, P, y);
+                        const unsigned m = __ballot_sync(kFull, ok);
+                        if (ok) Sc[count + __popc(m & lanemask_lt())] = y;
+                        count += __popc(m);
+                    }
+                } else {
+                    for (uint32_t base = 0; base < P; base += 32) {
+                        const uint32_t idx = base + lane;
+                        const bool valid = idx < P;
+                        const uint32_t y = valid ? Sp[idx] : 0u;
+                        const bool ok = valid && (!has_lo || y > lo) && lane_contains(g.col + start, L, y);
+                        const unsigned m = __ballot_sync(kFull, ok);
+                        if (ok) Sc[count + __popc(m & lanemask_lt())] = y;
+                        count += __popc(m);
+                    }
+                }
+                mat = true;
+            } else {
+                const uint32_t back = p.back[j];
+                const uint64_t key =
+                    ((int)lane < j && ((back >> lane) & 1u)) ? (((le - lb) << 5) | lane) : ~0ull;
+                const int driver = (int)(warp_min_u64(key) & 31u);
+                const uint64_t b = __shfl_sync(kFull, lb, driver);
+                const uint64_t en = __shfl_sync(kFull, le, driver);
+                const uint64_t start = has_lo ? b + warp_upper_bound(g.col + b, en - b, lo) : b;
+                for (uint64_t base = start; base < en; base += 32) {
+                    const uint64_t idx = base + lane;
+                    const bool valid = idx < en;
+                    const uint32_t y = valid ? __ldg(g.col + idx) : 0u;
+                    const bool ok = cand_ok(g, p, wm.v, j, driver, lb, le, y) && valid;
+                    const unsigned m = __ballot_sync(kFull, ok);
+                    if (ok) {
+                        const uint64_t pos = count + __popc(m & lanemask_lt());
+                        if (pos < a.cap) Sc[pos] = y;
+                    }
+                    count += __popc(m);
+                }
+                mat = count <= a.cap;
+                if (!mat && count > 0) {
+                    // second pass: locate the drawn element without storing the set
+                    const uint64_t target = index_map(r, count);
+                    uint64_t seen = 0;
+                    for (uint64_t base = start; base < en; base += 32) {
+                        const uint64_t idx = base + lane;
+                        const bool valid = idx < en;
+                        const uint32_t y = valid ? __ldg(g.col + idx) : 0u;
+                        const bool ok = cand_ok(g, p, wm.v, j, driver, lb, le, y) && valid;
+                        const unsigned m = __ballot_sync(kFull, ok);
+                        const uint64_t c = __popc(m);
+                        if (seen + c > target) {
+                            const uint32_t rank = (uint32_t)(target - seen);
+                            const bool mine = ok && (uint32_t)__popc(m & lanemask_lt()) == rank;
+                            const int src = __ffs(__ballot_sync(kFull, mine)) - 1;
+                            x = __shfl_sync(kFull, y, src);
+                            break;
+                        }
+                        seen += c;
+                    }
+                }
+            }
+            size = count;
+            if (lane == 0) wm.fac[j] = size;
+            if (size == 0) {
+                out.depth = j;
+                return out;
+            }
+            __syncwarp();
+            if (mat) x = Sc[index_map(r, size)];
+            prev_size = (uint32_t)(mat ? size : 0);
+            prev_mat = mat;
+        }
+        if (lane == 0) wm.v[j] = x;
+        if ((int)lane == j && j + 1 < k) {
+            lb = __ldg(g.row_ptr + x);
+            le = __ldg(g.row_ptr + x + 1);
+        }
+        __syncwarp();
+        w = __dmul_rn(w, (double)size);
+        if (__umul64hi(wu, size) != 0) ovf = true;
+        wu = wu * size;
+        out.depth = j + 1;
+    }
+    out.hit = true;
+    out.depth = k;
+    out.w = w;
+    out.wu = ovf ? 0 : wu;
+    out.overflow = ovf;
+    return out;
+}
+
+template <int MODE, bool TRACE>
+__global__ void __launch_bounds__(256) ns_kernel(const DGraph g, const Plan p, const RunArgs a) {
+    extern __shared__ uint64_t smem64[];
+    uint32_t *smem = reinterpret_cast<uint32_t *>(smem64);
+    const unsigned warp = threadIdx.x >> 5, lane = lane_id();
+    uint32_t *base = smem + warp * (kWarpHeaderWords + 2 * a.cap);
+    WarpMem wm;
+    wm.fac = reinterpret_cast<uint64_t *>(base);
+    wm.v = base + 24;
+    wm.S0 = base + kWarpHeaderWords;
+    wm.S1 = wm.S0 + a.cap;
+    const uint64_t end = a.first + a.count;
+    for (;;) {
+        unsigned c = 0;
+        if (lane == 0) c = atomicAdd(a.counter, 1u);
+        c = __shfl_sync(kFull, c, 0);
+        if (c >= a.nchunks) break;
+        const uint64_t s0 = a.first + (uint64_t)c * a.chunk;
+        const uint64_t s1 = (s0 + a.chunk < end) ? s0 + a.chunk : end;
+        double sum = 0.0, sumsq = 0.0;
+        uint64_t hits = 0;
+        for (uint64_t s = s0; s < s1; s++) {
+            if (TRACE && lane < kMaxK) wm.fac[lane] = 0;
+            __syncwarp();
+            const SampleOut r = sample_one<MODE>(g, p, a, s, wm);
+            if (r.hit) {
+                sum = __dadd_rn(sum, r.w);
+                sumsq = __dadd_rn(sumsq, __dmul_rn(r.w, r.w));
+                hits++;
+            }
+            if (TRACE) {
+                __syncwarp();
+                gpm_sample_record *rec = a.trace + (s - a.first);
+                if (lane < kMaxK) {
+                    rec->factor[lane] = wm.fac[lane];
+                    rec->vert[lane] = ((int)lane < r.depth && (int)lane < p.k) ? wm.v[lane] : 0xFFFFFFFFu;
+                    rec->aux[lane] = 0;
+                }
+                if (lane == 0) {
+                    rec->w_u64 = r.hit ? r.wu : 0;
+                    rec->w_f64 = r.hit ? r.w : 0.0;
+                    rec->hit = r.hit;
+                    rec->depth = (uint8_t)(r.hit ? p.k : r.depth);
+                    rec->overflow = r.overflow;
+                    for (int i = 0; i < 5; i++) rec->pad[i] = 0;
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0) {
+            Partial q;
+            q.sum = sum;
+            q.sumsq = sumsq;
+            q.hits = hits;
+            q.n = s1 - s0;
+            a.partials[c] = q;
+        }
+    }
+}
+
+// Adds the partials in chunk order (each thread a contiguous run, then a
+// fixed-shape tree) and folds them into the running totals.
+__global__ void __launch_bounds__(1024) reduce_partials(const Partial *__restrict__ parts, uint32_t n, Totals *tot,
+                                                        int accumulate) {
+    __shared__ double s_sum[1024], s_sq[1024];
+    __shared__ unsigned long long s_hits[1024], s_n[1024];
+    const unsigned t = threadIdx.x;
+    const uint32_t per = (n + 1023) / 1024;
+    const uint64_t b = (uint64_t)t * per;
+    const uint64_t e = (b + per < n) ? b + per : n;
+    double sum = 0.0, sq = 0.0;
+    unsigned long long hits = 0, cnt = 0;
+    for (uint64_t i = b; i < e; i++) {
+        sum = __dadd_rn(sum, parts[i].sum);
+        sq = __dadd_rn(sq, parts[i].sumsq);
+        hits += parts[i].hits;
+        cnt += parts[i].n;
+    }
+    s_sum[t] = sum;
+    s_sq[t] = sq;
+    s_hits[t] = hits;
+    s_n[t] = cnt;
+    __syncthreads();
+    for (unsigned h = 512; h; h >>= 1) {
+        if (t < h) {
+            s_sum[t] = __dadd_rn(s_sum[t], s_sum[t + h]);
+            s_sq[t] = __dadd_rn(s_sq[t], s_sq[t + h]);
+            s_hits[t] += s_hits[t + h];
+            s_n[t] += s_n[t + h];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        if (accumulate) {
+            tot->sum = __dadd_rn(tot->sum, s_sum[0]);
+            tot->sumsq = __dadd_rn(tot->sumsq, s_sq[0]);
+            tot->hits += s_hits[0];
+            tot->n += s_n[0];
+        } else {
+            tot->sum = s_sum[0];
+            tot->sumsq = s_sq[0];
+            tot->hits = s_hits[0];
+            tot->n = s_n[0];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+struct Shape {
+    uint32_t blocks, warps, cap, chunk;
+};
+
+static size_t smem_bytes(const Shape &sh) {
+    return (size_t)sh.warps * (kWarpHeaderWords + 2 * sh.cap) * sizeof(uint32_t);
+}
+
+template <int MODE, bool TRACE>
+static cudaError_t launch_ns(gpm_graph *h, const Plan &p, const Shape &sh, const RunArgs &a) {
+    auto kern = ns_kernel<MODE, TRACE>;
+    const size_t smem = smem_bytes(sh);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<sh.blocks, sh.warps * 32, smem, h->stream>>>(h->d, p, a);
+    return cudaGetLastError();
+}
+
+static Shape pick_shape(gpm_graph *h, const gpm_config *cfg, uint64_t count) {
+    Shape sh;
+    sh.warps = (cfg && cfg->block_warps) ? cfg->block_warps : 8;
+    sh.cap = (cfg && cfg->cap) ? cfg->cap : 512;
+    uint32_t per_sm = 6;
+    sh.blocks = (cfg && cfg->grid_blocks) ? cfg->grid_blocks : (uint32_t)h->sm_count * per_sm;
+    const uint64_t warps = (uint64_t)sh.blocks * sh.warps;
+    uint64_t chunk = count / (warps * 4);
+    if (chunk < 1) chunk = 1;
+    if (chunk > 256) chunk = 256;
+    sh.chunk = (uint32_t)chunk;
+    return sh;
+}
+
+static gpm_status ensure_partials(gpm_graph *h, uint64_t n) {
+    if (h->partials_cap >= n) return GPM_OK;
+    cudaFree(h->partials);
+    h->partials = nullptr;
+    h->partials_cap = 0;
+    if (cudaMalloc((void **)&h->partials, sizeof(Partial) * n) != cudaSuccess) {
+        set_error("device allocation of the per-chunk partials failed");
+        return GPM_ERR_OOM;
+    }
+    h->partials_cap = n;
+    return GPM_OK;
+}
+
+// One sampling launch over [first, first + count) plus the chunk-order
+// reduction into h->totals[0] (accumulate = fold into the running totals).
+static gpm_status run_block(gpm_graph *h, const Plan &p, int mode, uint64_t seed, uint32_t slot, uint64_t first,
+                            uint64_t count, const gpm_config *cfg, int accumulate, gpm_sample_record *trace,
+                            float *kernel_ms) {
+    Shape sh = pick_shape(h, cfg, count);
+    const uint64_t nchunks = (count + sh.chunk - 1) / sh.chunk;
+    if (nchunks >= (1ull << 31)) {
+        set_error("too many samples in one launch");
+        return GPM_ERR_ARG;
+    }
+    gpm_status st = ensure_partials(h, nchunks ? nchunks : 1);
+    if (st != GPM_OK) return st;
+    RunArgs a;
+    a.seed = seed;
+    a.first = first;
+    a.count = count;
+    a.partials = h->partials;
+    a.counter = h->counter;
+    a.trace = trace;
+    a.slot = slot;
+    a.cap = sh.cap;
+    a.chunk = sh.chunk;
+    a.nchunks = (uint32_t)nchunks;
+    if (cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), h->stream) != cudaSuccess) {
+        set_error("cudaMemsetAsync failed");
+        return GPM_ERR_CUDA;
+    }
+    if (kernel_ms) cudaEventRecord(h->ev0, h->stream);
+    cudaError_t e;
+    if (mode == MODE_CHECK)
+        e = trace ? launch_ns<MODE_CHECK, true>(h, p, sh, a) : launch_ns<MODE_CHECK, false>(h, p, sh, a);
+    else
+        e = trace ? launch_ns<MODE_INTERSECT, true>(h, p, sh, a) : launch_ns<MODE_INTERSECT, false>(h, p, sh, a);
+    if (kernel_ms) cudaEventRecord(h->ev1, h->stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("sampler launch: ") + cudaGetErrorString(e));
+        return GPM_ERR_CUDA;
+    }
+    reduce_partials<<<1, 1024, 0, h->stream>>>(h->partials, (uint32_t)nchunks, h->totals, accumulate);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->totals_host, h->totals, sizeof(Totals), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("sampling round: ") + cudaGetErrorString(e));
+        return GPM_ERR_CUDA;
+    }
+    if (kernel_ms) cudaEventElapsedTime(kernel_ms, h->ev0, h->ev1);
+    return GPM_OK;
+}
+
+static gpm_status plan_or_error(const gpm_pattern *pat, Plan *p) {
+    if (!pat) {
+        set_error("null pattern");
+        return GPM_ERR_ARG;
+    }
+    std::string why = build_plan(*pat, p);
+    if (!why.empty()) {
+        set_error("pattern rejected: " + why);
+        return GPM_ERR_ARG;
+    }
+    return GPM_OK;
+}
+
+static int mode_of(const gpm_config *cfg) { return (cfg && cfg->verify == GPM_VERIFY_CHECK) ? MODE_CHECK : MODE_INTERSECT; }
+
+// Phi^-1 by Newton iteration on the complementary error function, solved in
+// the lower tail (where erfc keeps full relative accuracy) and mirrored:
+// Phi(x) = erfc(-x / sqrt 2) / 2 and Phi'(x) = exp(-x^2 / 2) / sqrt(2 pi);
+// a bisection bracket on [-40, 0] gives the starting point.
+double normal_quantile(double p) {
+    if (!(p > 0.0 && p < 1.0)) return std::nan("");
+    const bool upper = p > 0.5;
+    const double q = upper ? 1.0 - p : p;
+    if (q == 0.5) return 0.0;
+    const double rs2 = 0.70710678118654752440;
+    double lo = -40.0, hi = 0.0;
+    for (int i = 0; i < 80 && hi - lo > 1e-3; i++) {
+        const double mid = 0.5 * (lo + hi);
+        if (0.5 * std::erfc(-mid * rs2) < q) lo = mid;
+        else hi = mid;
+    }
+    double x = 0.5 * (lo + hi);
+    const double inv_sqrt_2pi = 0.39894228040143267794;
+    for (int i = 0; i < 60; i++) {
+        const double c = 0.5 * std::erfc(-x * rs2);
+        const double d = inv_sqrt_2pi * std::exp(-0.5 * x * x);
+        if (d == 0.0) break;
+        const double step = (c - q) / d;
+        x -= step;
+        if (std::fabs(step) <= 1e-16 * std::fabs(x)) break;
+    }
+    return upper ? -x : x;
+}
+
+// Algorithm 3's end-of-window statistics.
+static void error_of(const Totals &t, double z, double *mu, double *half, double *eps_hat) {
+    const double n = (double)t.n;
+    const double m = t.sum / n;
+    double var = t.sumsq / n - m * m;
+    if (var < 0.0) var = 0.0;
+    const double sigma = std::sqrt(var / n);
+    *mu = m;
+    *half = z * sigma;
+    *eps_hat = (m > 0.0) ? z * sigma / m : INFINITY;
+}
+
+gpm_status ns_estimate(gpm_graph *h, const Plan &p, double eps, double delta, uint64_t seed,
+                       const gpm_config *cfg, gpm_result *out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const uint64_t W = (cfg && cfg->window) ? cfg->window : (1ull << 20);
+    const uint64_t n_min = (cfg && cfg->n_min) ? cfg->n_min : W;
+    const uint64_t n_max = (cfg && cfg->n_max) ? cfg->n_max : (1ull << 40);
+    const double max_s = cfg ? cfg->max_seconds : 0.0;
+    const uint32_t slot = cfg ? cfg->slot : 0;
+    const int mode = mode_of(cfg);
+    if (!(eps > 0.0) || !(delta > 0.0 && delta < 1.0)) {
+        set_error("eps must be > 0 and delta in (0, 1)");
+        return GPM_ERR_ARG;
+    }
+    const double z = normal_quantile(1.0 - delta / 2.0);
+    h->abort_flag = 0;
+    double t_kernel = 0.0;
+    gpm_status status = GPM_OK;
+    uint64_t rounds = 0;
+    for (;;) {
+        float ms = 0.f;
+        gpm_status st = run_block(h, p, mode, seed, slot, rounds * W, W, cfg, rounds > 0, nullptr, &ms);
+        if (st != GPM_OK) return st;
+        rounds++;
+        t_kernel += ms * 1e-3;
+        out->kernel_launches += 2;
+        const Totals &t = *h->totals_host;
+        double mu, half, eh;
+        error_of(t, z, &mu, &half, &eh);
+        out->estimate = mu;
+        out->ci_half_width = half;
+        out->eps_hat = eh;
+        out->sum = t.sum;
+        out->sumsq = t.sumsq;
+        out->samples = t.n;
+        out->hits = t.hits;
+        out->rounds = rounds;
+        if (t.n >= n_min && mu > 0.0 && eh <= eps) {
+            out->converged = 1;
+            break;
+        }
+        if (t.n >= n_max) {
+            status = GPM_ERR_NOT_CONVERGED;
+            set_error("n_max reached before eps_hat <= eps");
+            break;
+        }
+        if (h->abort_flag) {
+            status = GPM_ERR_ABORTED;
+            set_error("aborted");
+            break;
+        }
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (max_s > 0.0 && el >= max_s) {
+            status = GPM_ERR_NOT_CONVERGED;
+            set_error("max_seconds reached before eps_hat <= eps");
+            break;
+        }
+    }
+    out->scheme_used = GPM_NS;
+    out->t_sample_s = t_kernel;
+    out->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return status;
+}
+
+}  // namespace gpm
+
+using namespace gpm;
+
+extern "C" gpm_status gpm_sample_sums(gpm_graph *h, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
+                                      uint64_t count, const gpm_config *cfg, gpm_sums *out) {
+    if (!h || !out) {
+        set_error("gpm_sample_sums: null argument");
+        return GPM_ERR_ARG;
+    }
+    Plan p;
+    gpm_status st = plan_or_error(pattern, &p);
+    if (st != GPM_OK) return st;
+    std::memset(out, 0, sizeof(*out));
+    if (count == 0) return GPM_OK;
+    st = run_block(h, p, mode_of(cfg), seed, cfg ? cfg->slot : 0, first, count, cfg, 0, nullptr, nullptr);
+    if (st != GPM_OK) return st;
+    out->n = h->totals_host->n;
+    out->hits = h->totals_host->hits;
+    out->sum = h->totals_host->sum;
+    out->sumsq = h->totals_host->sumsq;
+    return GPM_OK;
+}
+
+extern "C" gpm_status gpm_trace(gpm_graph *h, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
+                                uint64_t count, const gpm_config *cfg, gpm_sample_record *out) {
+    if (!h || (!out && count)) {
+        set_error("gpm_trace: null argument");
+        return GPM_ERR_ARG;
+    }
+    Plan p;
+    gpm_status st = plan_or_error(pattern, &p);
+    if (st != GPM_OK) return st;
+    if (count == 0) return GPM_OK;
+    gpm_sample_record *d = nullptr;
+    if (cudaMalloc((void **)&d, sizeof(gpm_sample_record) * count) != cudaSuccess) {
+        set_error("gpm_trace: device allocation failed");
+        return GPM_ERR_OOM;
+    }
+    st = run_block(h, p, mode_of(cfg), seed, cfg ? cfg->slot : 0, first, count, cfg, 0, d, nullptr);
+    if (st == GPM_OK) {
+        cudaError_t e = cudaMemcpy(out, d, sizeof(gpm_sample_record) * count, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            set_error(std::string("gpm_trace: copy back: ") + cudaGetErrorString(e));
+            st = GPM_ERR_CUDA;
+        }
+    }
+    cudaFree(d);
+    return st;
+}
+
+extern "C" gpm_status gpm_plan(const gpm_pattern *pattern, int32_t *order, int32_t *res_lo, int32_t *res_hi,
+                               int32_t *nres, int32_t *oriented) {
+    Plan p;
+    gpm_status st = plan_or_error(pattern, &p);
+    if (st != GPM_OK) return st;
+    if (order)
+        for (int j = 0; j < p.k; j++) order[j] = p.order[j];
+    if (res_lo && res_hi)
+        for (int r = 0; r < p.nres; r++) {
+            res_lo[r] = p.res_lo[r];
+            res_hi[r] = p.res_hi[r];
+        }
+    if (nres) *nres = p.nres;
+    if (oriented) *oriented = p.oriented;
+    return GPM_OK;
+}
+
+extern "C" double gpm_normal_quantile(double p) { return normal_quantile(p); }
+
+extern "C" gpm_status gpm_estimate(gpm_graph *h, const gpm_pattern *pattern, gpm_scheme scheme, double eps,
+                                   double delta, uint64_t seed, const gpm_config *cfg, gpm_result *out) {
+    if (!h || !out) {
+        set_error("gpm_estimate: null argument");
+        return GPM_ERR_ARG;
+    }
+    std::memset(out, 0, sizeof(*out));
+    Plan p;
+    gpm_status st = plan_or_error(pattern, &p);
+    if (st != GPM_OK) return st;
+    switch (scheme) {
+        case GPM_NS:
+            return ns_estimate(h, p, eps, delta, seed, cfg, out);
+        default:
+            set_error("gpm_estimate: scheme not available in this build");
+            return GPM_ERR_UNSUPPORTED;
+    }
+}

@@ -1,0 +1,174 @@
+"""GPU parity of the NS sampler (INTERSECT and CHECK verify) against the CPU
+oracle, through the C ABI: per-sample records bit-exact, FP64 aggregates
+within 1e-12 relative, the online stopping rule on the same samples."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2405_03488_gb300 import api
+from paper_2405_03488_gb300 import graphs as G
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12   # FP64 reduction-order tolerance of aggregates
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2405_03488_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def pair(rp, col):
+    """(GPU handle borrowing CUDA tensors, oracle graph on the host copy)."""
+    g = api.Graph(rp.cuda(), col.cuda(), validate=True)
+    return g, O.Graph(*G.to_numpy(rp, col))
+
+
+def assert_same_records(gpu, cpu, k):
+    assert len(gpu) == len(cpu)
+    for f in ("hit", "depth", "w_u64", "overflow"):
+        bad = np.nonzero(gpu[f] != cpu[f])[0]
+        assert len(bad) == 0, (f, bad[:5], gpu[f][bad[:5]], cpu[f][bad[:5]])
+    assert np.array_equal(gpu["w_f64"].view(np.uint64), cpu["w_f64"].view(np.uint64))
+    assert np.array_equal(gpu["factor"][:, :k], cpu["factor"][:, :k])
+    assert np.array_equal(gpu["vert"][:, :k], cpu["vert"][:, :k])
+
+
+PATTERNS = [("triangle", False), ("4-clique", False), ("5-clique", False), ("4-cycle", False),
+            ("4-cycle", True), ("diamond", False), ("tailed-triangle", True), ("3-star", True),
+            ("4-path", False), ("house", False), ("5-path", True), ("edge", False)]
+
+
+@pytest.mark.parametrize("verify", ["intersect", "check"])
+@pytest.mark.parametrize("name,induced", PATTERNS)
+def test_trace_bit_exact_small(name, induced, verify):
+    rp, col = G.erdos_renyi(40, 0.3, seed=3)
+    g, og = pair(rp, col)
+    k, edges = G.pattern(name)
+    pat = (k, edges, induced)
+    mode = O.CHECK if verify == "check" else O.INTERSECT
+    first, count = 12345, 3001
+    gpu = g.trace(pat, seed=77, first=first, count=count, verify=verify)
+    _, cpu = O.ns_run(og, O.plan(k, edges, induced), seed=77, first=first, count=count, mode=mode, trace=True)
+    assert_same_records(gpu, cpu, k)
+    assert gpu["hit"].sum() > 0
+
+
+@pytest.mark.parametrize("cap,warps,blocks", [(1, 1, 3), (4, 2, 5), (33, 8, 7), (512, 4, 0)])
+def test_two_pass_and_odd_shapes_bit_exact(cap, warps, blocks):
+    # dense graph: candidate sets overflow the small on-chip buffers
+    rp, col = G.erdos_renyi(80, 0.5, seed=5)
+    g, og = pair(rp, col)
+    for name, induced in (("4-clique", False), ("4-cycle", False), ("diamond", True), ("5-clique", False)):
+        k, edges = G.pattern(name)
+        gpu = g.trace((k, edges, induced), seed=9, first=0, count=1500, cap=cap, block_warps=warps,
+                      grid_blocks=blocks)
+        _, cpu = O.ns_run(og, O.plan(k, edges, induced), seed=9, first=0, count=1500, trace=True)
+        assert_same_records(gpu, cpu, k)
+
+
+def test_sums_match_oracle_er_triangle_1e6():
+    """ER G(n=10^4, p=0.002), triangle, 10^6 samples, seed 1."""
+    rp, col = G.erdos_renyi(10_000, 0.002, seed=1)
+    g, og = pair(rp, col)
+    p = O.plan(*G.pattern("triangle"))
+    N = 1_000_000
+    s = g.sample_sums("triangle", seed=1, first=0, count=N)
+    acc, _ = O.ns_run(og, p, seed=1, first=0, count=N)
+    assert s.n == N and s.hits == acc.hits
+    assert s.sum == pytest.approx(acc.sum, rel=REL)
+    assert s.sumsq == pytest.approx(acc.sumsq, rel=REL)
+    exact = O.exact_count(og, p)
+    mean = s.sum / N
+    sd = math.sqrt((s.sumsq / N - mean * mean) / N)
+    assert abs(mean - exact) < 5 * sd
+
+
+@pytest.mark.parametrize("verify", ["intersect", "check"])
+def test_online_matches_oracle(verify):
+    rp, col = G.erdos_renyi(3000, 0.01, seed=2)
+    g, og = pair(rp, col)
+    mode = O.CHECK if verify == "check" else O.INTERSECT
+    for name, eps in (("triangle", 0.02), ("4-cycle", 0.05)):
+        k, edges = G.pattern(name)
+        W = 1 << 15
+        r = g.estimate(name, eps=eps, delta=0.01, seed=4, window=W, verify=verify)
+        o = O.ns_online(og, O.plan(k, edges), eps, 0.01, seed=4, window=W, mode=mode)
+        assert r["converged"] == o.converged == 1
+        assert r["samples"] == o.samples and r["rounds"] == o.rounds and r["hits"] == o.hits
+        assert r["estimate"] == pytest.approx(o.estimate, rel=REL)
+        assert r["eps_hat"] == pytest.approx(o.eps_hat, rel=1e-10)
+        assert r["ci_half_width"] == pytest.approx(o.ci_half_width, rel=1e-10)
+
+
+def test_edge_cases():
+    # no edges at all: every sample misses, mu = 0, never converges
+    rp, col = G.from_edge_list(6, [])
+    g = api.Graph(rp.cuda(), col.cuda())
+    r = g.estimate("triangle", eps=0.1, delta=0.1, seed=1, window=1000, n_max=3000)
+    assert r["estimate"] == 0.0 and r["converged"] == 0 and r["samples"] == 3000
+    tr = g.trace("triangle", seed=1, first=0, count=10)
+    assert tr["hit"].sum() == 0 and np.all(tr["depth"] == 0)
+    # one-edge pattern: weight m on every sample, exact at once
+    rp, col = G.complete(9)
+    g = api.Graph(rp.cuda(), col.cuda())
+    r = g.estimate("edge", eps=0.01, delta=0.01, seed=1, window=100)
+    assert r["estimate"] == 36.0 and r["eps_hat"] == 0.0 and r["rounds"] == 1
+    # isolated vertices, ragged counts, a far sample offset
+    rp, col = G.from_edge_list(50, [(1, 7), (7, 9), (1, 9), (9, 30), (30, 1), (7, 30), (44, 45)])
+    g, og = pair(rp, col)
+    for count in (1, 31, 33, 1023):
+        for first in (0, 2**40 + 5):
+            gpu = g.trace("4-clique", seed=3, first=first, count=count)
+            _, cpu = O.ns_run(og, O.plan(*G.clique(4)), seed=3, first=first, count=count, trace=True)
+            assert_same_records(gpu, cpu, 4)
+            s = g.sample_sums("4-clique", seed=3, first=first, count=count)
+            acc, _ = O.ns_run(og, O.plan(*G.clique(4)), seed=3, first=first, count=count)
+            assert (s.n, s.hits) == (acc.n, acc.hits) and s.sum == pytest.approx(acc.sum, rel=REL)
+
+
+def test_validation_rejects_bad_csr():
+    from paper_2405_03488_gb300 import _lib
+    rp, col = G.complete(5)
+    bad = col.clone()
+    bad[0], bad[1] = bad[1].item(), bad[0].item()     # unsorted
+    with pytest.raises(_lib.GpmError) as e:
+        api.Graph(rp.cuda(), bad.cuda(), validate=True)
+    assert e.value.code == _lib.GPM_ERR_GRAPH
+    asym_rp = torch.tensor([0, 1, 1], dtype=torch.int64)
+    with pytest.raises(_lib.GpmError):
+        api.Graph(asym_rp.cuda(), torch.tensor([1], dtype=torch.int32).cuda(), validate=True)
+    # host arrays are copied, and a valid graph passes
+    g = api.Graph(rp.numpy(), col.numpy(), validate=True)
+    assert (g.n, g.m, g.nnz, g.max_degree) == (5, 10, 20, 4)
+
+
+@pytest.fixture(scope="module")
+def rmat22():
+    rp, col = G.rmat(22, 16, seed=2, device="cuda")
+    return rp, col
+
+
+@pytest.mark.parametrize("name", ["4-clique", "5-clique"])
+def test_rmat22_sampled_parity_in_bench_shape(rmat22, name):
+    """R-MAT scale 22 (the benchmark workload): records of sample ranges deep
+    into a run are bit-exact, in the launch shape the benchmark uses."""
+    rp, col = rmat22
+    g = api.Graph(rp, col)
+    og = O.Graph(*G.to_numpy(rp, col))
+    k, edges = G.pattern(name)
+    p = O.plan(k, edges)
+    for first in (0, 987_654_321):
+        gpu = g.trace(name, seed=1, first=first, count=20_000)
+        _, cpu = O.ns_run(og, p, seed=1, first=first, count=20_000, trace=True)
+        assert_same_records(gpu, cpu, k)
+        assert gpu["hit"].sum() > 0
+    s = g.sample_sums(name, seed=1, first=1 << 20, count=1 << 18)
+    acc, _ = O.ns_run(og, p, seed=1, first=1 << 20, count=1 << 18)
+    assert (s.n, s.hits) == (acc.n, acc.hits)
+    assert s.sum == pytest.approx(acc.sum, rel=REL) and s.sumsq == pytest.approx(acc.sumsq, rel=REL)
