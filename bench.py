@@ -1,0 +1,346 @@
+"""Benchmark: time-to-converge at +-1% with 99% confidence, and samples/s, of
+neighbour sampling with eager verify on R-MAT scale 22 (edge factor 16),
+4-clique and 5-clique, through libgpm's C ABI on one GB300.
+
+A step is one full estimate of each pattern to eps = 1%, delta = 1%
+(Algorithm 3 rounds of 2^20 samples until eps_hat <= eps), seed = step index.
+``value`` = samples/s over the timed steps with the graph resident in HBM;
+``e2e`` repeats the steps through the public API from pinned host arrays
+(graph upload and result read-back inside the timed region).
+
+--impl reference times the CPU oracle (the reference arm of this project) on
+the host cores over a bounded sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PATTERNS = ("4-clique", "5-clique")
+EPS, DELTA = 0.01, 0.01
+N_MAX = 1_000_000_000
+WINDOW = 1 << 20
+SCALE, EDGE_FACTOR, GRAPH_SEED = 22, 16, 2
+METRIC = "time-to-converge (+-1% @99% conf) and samples/s, learned vs plain NS"
+WORKLOAD = "R-MAT scale 22, edge factor 16 (a,b,c = 0.57,0.19,0.19), 4-clique + 5-clique NS eager-verify"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpm", choices=["gpm", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workload
+def make_graph(device):
+    from paper_2405_03488_gb300 import graphs as G
+    return G.rmat(SCALE, EDGE_FACTOR, seed=GRAPH_SEED, device=device)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """Per-launch DRAM traffic of the sampler from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    import hashlib
+    summ = os.path.join(ROOT, "profiles", "ns_kernel_rmat22.md")
+    src = os.path.join(ROOT, "paper_2405_03488_gb300", "csrc", "ns.cu")
+    if not os.path.exists(summ):
+        return None
+    txt = open(summ).read()
+    m1 = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    m2 = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.e+]+)", txt)
+    if not (m1 and m2):
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != m1.group(1):
+        return None
+    return float(m2.group(1))
+
+
+# ------------------------------------------------------------------ CPU oracle (cpu_baseline / reference arm)
+def _oracle_worker(args):
+    rp_path, col_path, name, seed, first, count = args
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    from paper_2405_03488_gb300 import graphs as G
+    rp = np.load(rp_path, mmap_mode="r")
+    col = np.load(col_path, mmap_mode="r")
+    g = O.Graph(rp, col)
+    k, edges = G.pattern(name)
+    p = O.plan(k, edges)
+    t0 = time.perf_counter()
+    acc, _ = O.ns_run(g, p, seed=seed, first=first, count=count, want_bytes=True)
+    dt = time.perf_counter() - t0
+    return name, acc.n, acc.hits, acc.sum, acc.sumsq, acc.bytes, dt
+
+
+def oracle_sample(rp_np, col_np, budget_s, seed=1):
+    """Runs the oracle as it stands over a bounded prefix of each pattern's
+    sample stream, split across the host cores (spawned processes).  Returns
+    per-pattern totals and the wall time."""
+    import multiprocessing as mp
+    import numpy as np
+    tmp = tempfile.mkdtemp(prefix="gpm_oracle_")
+    rp_path, col_path = os.path.join(tmp, "rp.npy"), os.path.join(tmp, "col.npy")
+    np.save(rp_path, rp_np)
+    np.save(col_path, col_np)
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    out = {}
+    with ctx.Pool(cores) as pool:
+        # calibrate: a short single-process run per pattern
+        rate = {}
+        for name in PATTERNS:
+            r = pool.apply(_oracle_worker, ((rp_path, col_path, name, seed, 0, 4000),))
+            rate[name] = r[1] / max(r[6], 1e-6)
+        t0 = time.perf_counter()
+        jobs = []
+        for name in PATTERNS:
+            per_core = max(1000, int(rate[name] * budget_s / len(PATTERNS)))
+            for c in range(cores):
+                jobs.append((rp_path, col_path, name, seed, c * per_core, per_core))
+        res = pool.map(_oracle_worker, jobs)
+        wall = time.perf_counter() - t0
+    for name in PATTERNS:
+        rows = [r for r in res if r[0] == name]
+        out[name] = {"n": sum(r[1] for r in rows), "hits": sum(r[2] for r in rows),
+                     "sum": sum(r[3] for r in rows), "bytes": sum(r[5] for r in rows)}
+    for pth in (rp_path, col_path):
+        os.unlink(pth)
+    os.rmdir(tmp)
+    return out, wall, cores
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on the host cores, same metric and config."""
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    import torch
+    from paper_2405_03488_gb300 import graphs as G
+    rp, col = make_graph("cpu")
+    rp_np, col_np = G.to_numpy(rp, col)
+    del rp, col
+    budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(rp_np, col_np, min(budget, 2.0))
+    tot_n, tot_t = 0, 0.0
+    cores = 1
+    for step in range(args.steps):
+        res, wall, cores = oracle_sample(rp_np, col_np, budget, seed=step + 1)
+        tot_n += sum(v["n"] for v in res.values())
+        tot_t += wall
+    value = tot_n / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "patterns": list(PATTERNS), "eps": EPS, "delta": DELTA,
+                       "window": WINDOW, "l2": "inputs larger than L2 (0.5 GB CSR)"},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                             "sample": "per step about %.0f s of oracle work: a prefix of each pattern's "
+                                       "sample stream split over %d spawned processes" % (budget, cores)},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_03488_gb300 import api
+    from paper_2405_03488_gb300 import graphs as G
+
+    rp, col = make_graph("cuda")
+    torch.cuda.synchronize()
+    g = api.Graph(rp, col)
+    n, m, nnz = g.n, g.m, g.nnz
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def one_step(graph, step):
+        res = {}
+        for name in PATTERNS:
+            # weak scaling: every rank runs its own estimate on its own seed stream
+            res[name] = graph.estimate(name, eps=EPS, delta=DELTA, seed=1 + step + 1000 * rank,
+                                       window=WINDOW, n_max=N_MAX)
+        return res
+
+    for w in range(args.warmup):
+        one_step(g, w)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    per_step = []
+    for s in range(args.steps):
+        per_step.append(one_step(g, s))
+    ev1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    barrier()
+    samples = sum(r[p]["samples"] for r in per_step for p in PATTERNS)
+    kernel_s = sum(r[p]["t_sample_s"] for r in per_step for p in PATTERNS)
+    rounds = sum(r[p]["rounds"] for r in per_step for p in PATTERNS)
+    launches = sum(r[p]["kernel_launches"] for r in per_step for p in PATTERNS)
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+        sm = torch.tensor([samples], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(sm)
+        samples_all = float(sm.item())
+    else:
+        samples_all = samples
+    value = samples_all / elapsed
+
+    # end to end through the public API from pinned host memory
+    rp_h = rp.cpu().pin_memory()
+    col_h = col.cpu().pin_memory()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_samples, e2e_d2h = 0, 0
+    for s in range(args.steps):
+        gh = api.Graph(rp_h.numpy().view(np.uint64), col_h.numpy().view(np.uint32))
+        r = one_step(gh, s)
+        gh.close()
+        e2e_samples += sum(r[p]["samples"] for p in PATTERNS)
+        e2e_d2h += sum(r[p]["rounds"] for p in PATTERNS) * 32 + 32
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    e2e = {"value": e2e_samples * world / e2e_t, "unit": "samples/s",
+           "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz, "d2h_bytes_per_step": e2e_d2h // args.steps}
+
+    if rank != 0:
+        return
+    last = per_step[-1]
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "m": m, "patterns": list(PATTERNS), "eps": EPS,
+                       "delta": DELTA, "window": WINDOW, "n_max": N_MAX,
+                       "l2": "inputs larger than L2 (CSR %.2f GB vs 129 MB L2)" % ((8 * (n + 1) + 4 * nnz) / 1e9)},
+            "time_to_converge_s": {p: last[p]["t_total_s"] for p in PATTERNS},
+            "samples_to_converge": {p: last[p]["samples"] for p in PATTERNS},
+            "estimate": {p: last[p]["estimate"] for p in PATTERNS},
+            "eps_hat": {p: last[p]["eps_hat"] for p in PATTERNS},
+            "hit_rate": {p: last[p]["hits"] / max(1, last[p]["samples"]) for p in PATTERNS},
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": ck}
+
+    peak, peak_kind = measured_peaks()
+    roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
+            "traffic": ncu_traffic(), "kernel": "ns_kernel<INTERSECT>", "peak_kind": peak_kind}
+    if world == 1 and not args.no_cpu_baseline:
+        ores, wall, cores = oracle_sample(*G.to_numpy(rp, col), args.cpu_seconds)
+        cpu_n = sum(v["n"] for v in ores.values())
+        line["cpu_baseline"] = {"value": cpu_n / wall, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                                "sample": "%d samples (prefix of each pattern's seed-1 stream, %s) split over %d "
+                                          "spawned processes" % (cpu_n, "+".join(PATTERNS), cores)}
+        # algorithmic bytes per sample from the oracle's per-sample accounting
+        bbar = {p: ores[p]["bytes"] / ores[p]["n"] for p in PATTERNS}
+        algo_bytes = sum(bbar[p] * r[p]["samples"] for r in per_step for p in PATTERNS)
+        achieved = algo_bytes / kernel_s / 1e9
+        roof.update({"achieved": achieved, "frac": achieved / peak if peak else None,
+                     "bytes_per_sample": bbar, "launches": int(rounds),
+                     "avg_launch_ms": 1e3 * kernel_s / max(1, rounds)})
+    line["roofline"] = roof
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,17 +1,367 @@
-// Colour sparsification and exact counting (filled in below the NS path).
+// Colour sparsification (GS) and exact counting.
+//
+// Colour sparsification (Sec. 2.2.2): every vertex gets a colour in [0, c)
+// and only monochromatic edges stay; a match with k vertices survives iff its
+// vertices share one colour, with probability c^-(k-1), so the exact count C'
+// of the sparsified graph scaled by c^(k-1) is an unbiased estimate of C
+// (Sec. 5.2; the paper writes the exponent with the edge count, which only
+// agrees for triangles).  colour(v) = floor(w0 * c / 2^32), w0 the first word
+// of Philox4x32-10 at counter (v_lo, v_hi, colouring, slot << 8 | 2), key =
+// seed, a stream disjoint from the sampling words.
+//
+// Sparsification reads every edge once and writes the kept ones (the paper's
+// preprocessing cost |E| (w1 + p w2), Sec. 4.4): a colour pass, a count pass
+// and a compaction pass (one warp per vertex, ballot compaction keeps the
+// neighbour order), with the row offsets from the library's prefix scan.
+//
+// Exact counting runs the same plan as the sampler but follows every branch
+// (the nested loops of Sec. 4.4): one warp walks the subtree of one first edge
+// depth first; each level keeps its driver-list cursor and one 32-entry chunk
+// of candidates on chip, so no level needs more than 32 slots, and the last
+// level only counts |S_{k-1}|.  Per-warp totals are added with 64-bit atomics
+// (exact integers, order independent).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "device.cuh"
 #include "internal.h"
+
+namespace gpm {
+
+cudaError_t scan_exclusive_u64(const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t st);
+
+__global__ void colour_kernel(uint64_t n, uint32_t c, uint64_t seed, uint32_t colouring, uint32_t slot,
+                              uint32_t *colours) {
+    const uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const Philox4 o = philox10((uint32_t)v, (uint32_t)(v >> 32), colouring, (slot << 8) | 2u, (uint32_t)seed,
+                               (uint32_t)(seed >> 32));
+    colours[v] = (uint32_t)(((uint64_t)o.x * (uint64_t)c) >> 32);
+}
+
+__global__ void keep_count(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
+                           const uint32_t *__restrict__ colours, uint64_t n, uint64_t *cnt) {
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const unsigned lane = threadIdx.x & 31u;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = warp; v < n; v += nw) {
+        const uint64_t b = row_ptr[v], e = row_ptr[v + 1];
+        const uint32_t cv = colours[v];
+        uint64_t c = 0;
+        for (uint64_t i = b + lane; i < e; i += 32) c += (colours[__ldg(col + i)] == cv);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+        if (lane == 0) cnt[v] = c;
+    }
+}
+
+__global__ void keep_write(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
+                           const uint32_t *__restrict__ colours, uint64_t n, const uint64_t *__restrict__ row_out,
+                           uint32_t *col_out) {
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const unsigned lane = threadIdx.x & 31u;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = warp; v < n; v += nw) {
+        const uint64_t b = row_ptr[v], e = row_ptr[v + 1];
+        const uint32_t cv = colours[v];
+        uint64_t pos = row_out[v];
+        for (uint64_t base = b; base < e; base += 32) {
+            const uint64_t i = base + lane;
+            const uint32_t x = i < e ? __ldg(col + i) : 0u;
+            const bool keep = i < e && colours[x] == cv;
+            const unsigned m = __ballot_sync(kFull, keep);
+            if (keep) col_out[pos + __popc(m & ((1u << lane) - 1u))] = x;
+            pos += __popc(m);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ exact count
+struct Level {
+    uint64_t base, end;      // driver cursor and end
+    uint32_t mask;           // candidates of the current chunk not yet visited
+    int32_t driver;
+};
+
+__device__ __forceinline__ bool exact_ok(const DGraph &g, const Plan &p, const uint32_t *v, int j, int driver,
+                                         uint64_t lb, uint64_t le, uint32_t x) {
+    bool ok = true;
+    const uint32_t back = p.back[j];
+    for (int i = 0; i < j; i++) {
+        const uint64_t b = __shfl_sync(kFull, lb, i);
+        const uint64_t e = __shfl_sync(kFull, le, i);
+        ok = ok && (x != v[i]);
+        const bool edge = (back >> i) & 1u;
+        if (edge && i != driver) ok = ok && lane_contains(g.col + b, e - b, x);
+        else if (!edge && p.induced) ok = ok && !lane_contains(g.col + b, e - b, x);
+    }
+    return ok;
+}
+
+// Driver (shortest back-neighbour list) and its range above the lower bound.
+__device__ __forceinline__ void level_init(const DGraph &g, const Plan &p, const uint32_t *v, int j, uint64_t lb,
+                                           uint64_t le, Level *L) {
+    const unsigned lane = lane_id();
+    const uint32_t back = p.back[j];
+    uint64_t key = ((int)lane < j && ((back >> lane) & 1u)) ? (((le - lb) << 5) | lane) : ~0ull;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        uint64_t t = __shfl_xor_sync(kFull, key, o);
+        key = t < key ? t : key;
+    }
+    const int d = (int)(key & 31u);
+    const uint64_t b = __shfl_sync(kFull, lb, d);
+    const uint64_t e = __shfl_sync(kFull, le, d);
+    const uint32_t lm = p.lower[j];
+    uint32_t lo = 0;
+    for (int i = 0; i < j; i++)
+        if ((lm >> i) & 1u) lo = v[i] > lo ? v[i] : lo;
+    const uint64_t start = lm ? b + warp_upper_bound(g.col + b, e - b, lo) : b;
+    if (lane == 0) {
+        L->base = start;
+        L->end = e;
+        L->mask = 0;
+        L->driver = d;
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(256) exact_kernel(const DGraph g, const Plan p, uint64_t M, unsigned int *counter,
+                                                    uint32_t per_grab, unsigned long long *total) {
+    __shared__ Level lev[8][kMaxK];
+    __shared__ uint32_t vv[8][kMaxK];
+    __shared__ uint32_t buf[8][kMaxK][32];
+    const unsigned warp = threadIdx.x >> 5, lane = lane_id();
+    Level *L = lev[warp];
+    uint32_t *v = vv[warp];
+    const int k = p.k;
+    unsigned long long acc = 0;
+    for (;;) {
+        unsigned grab = 0;
+        if (lane == 0) grab = atomicAdd(counter, 1u);
+        grab = __shfl_sync(kFull, grab, 0);
+        const uint64_t e0 = (uint64_t)grab * per_grab;
+        if (e0 >= M) break;
+        const uint64_t e1 = (e0 + per_grab < M) ? e0 + per_grab : M;
+        for (uint64_t e = e0; e < e1; e++) {
+            uint32_t v0, v1;
+            if (p.oriented) {
+                const uint64_t u = warp_upper_bound(g.uoff, g.n + 1, e) - 1;
+                v0 = (uint32_t)u;
+                v1 = __ldg(g.col + __ldg(g.up + u) + (e - __ldg(g.uoff + u)));
+            } else {
+                const uint64_t u = warp_upper_bound(g.row_ptr, g.n + 1, e) - 1;
+                v0 = (uint32_t)u;
+                v1 = __ldg(g.col + e);
+            }
+            if (k == 2) {
+                acc += 1;
+                continue;
+            }
+            uint64_t lb = 0, le = 0;
+            if (lane == 0) {
+                lb = __ldg(g.row_ptr + v0);
+                le = __ldg(g.row_ptr + v0 + 1);
+                v[0] = v0;
+                v[1] = v1;
+            } else if (lane == 1) {
+                lb = __ldg(g.row_ptr + v1);
+                le = __ldg(g.row_ptr + v1 + 1);
+            }
+            __syncwarp();
+            int j = 2;
+            level_init(g, p, v, j, lb, le, &L[j]);
+            while (j >= 2) {
+                Level &cur = L[j];
+                const bool last = (j == k - 1);
+                if (cur.mask == 0 || last) {
+                    if (cur.base >= cur.end) {
+                        j--;
+                        continue;
+                    }
+                    const uint64_t idx = cur.base + lane;
+                    const bool valid = idx < cur.end;
+                    const uint32_t y = valid ? __ldg(g.col + idx) : 0u;
+                    const bool ok = exact_ok(g, p, v, j, cur.driver, lb, le, y) && valid;
+                    const unsigned m = __ballot_sync(kFull, ok);
+                    if (last) {
+                        acc += __popc(m);
+                    } else {
+                        buf[warp][j][lane] = y;
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        cur.base += 32;
+                        cur.mask = last ? 0u : m;
+                    }
+                    __syncwarp();
+                    continue;
+                }
+                const uint32_t m = cur.mask;
+                const int bit = __ffs(m) - 1;
+                const uint32_t x = buf[warp][j][bit];
+                __syncwarp();
+                if (lane == 0) {
+                    cur.mask = m & (m - 1u);
+                    v[j] = x;
+                }
+                if ((int)lane == j) {
+                    lb = __ldg(g.row_ptr + x);
+                    le = __ldg(g.row_ptr + x + 1);
+                }
+                __syncwarp();
+                j++;
+                level_init(g, p, v, j, lb, le, &L[j]);
+            }
+        }
+    }
+    if (lane == 0 && acc) atomicAdd(total, acc);
+}
+
+}  // namespace gpm
 
 using namespace gpm;
 
-extern "C" gpm_status gpm_exact_count(gpm_graph *, const gpm_pattern *, uint64_t *) {
-    set_error("gpm_exact_count: not built yet");
-    return GPM_ERR_UNSUPPORTED;
+namespace gpm {
+
+gpm_status exact_count_plan(gpm_graph *h, const Plan &p, uint64_t *out, float *kernel_ms) {
+    const uint64_t M = p.oriented ? h->d.m : h->d.nnz;
+    unsigned long long *tot = nullptr;
+    unsigned int *ctr = nullptr;
+    if (cudaMallocAsync((void **)&tot, sizeof(unsigned long long), h->stream) != cudaSuccess ||
+        cudaMallocAsync((void **)&ctr, sizeof(unsigned int), h->stream) != cudaSuccess) {
+        set_error("exact count: device allocation failed");
+        return GPM_ERR_OOM;
+    }
+    cudaMemsetAsync(tot, 0, sizeof(unsigned long long), h->stream);
+    cudaMemsetAsync(ctr, 0, sizeof(unsigned int), h->stream);
+    uint64_t per = M / ((uint64_t)h->sm_count * 8 * 8 * 64) + 1;
+    if (per > 64) per = 64;
+    if (M / per >= (1ull << 32)) per = M / (1ull << 31) + 1;
+    if (kernel_ms) cudaEventRecord(h->ev0, h->stream);
+    if (M > 0) exact_kernel<<<h->sm_count * 8, 256, 0, h->stream>>>(h->d, p, M, ctr, (uint32_t)per, tot);
+    if (kernel_ms) cudaEventRecord(h->ev1, h->stream);
+    cudaError_t e = cudaGetLastError();
+    unsigned long long r = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&r, tot, sizeof(r), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFreeAsync(tot, h->stream);
+    cudaFreeAsync(ctr, h->stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("exact count: ") + cudaGetErrorString(e));
+        return GPM_ERR_CUDA;
+    }
+    if (kernel_ms) cudaEventElapsedTime(kernel_ms, h->ev0, h->ev1);
+    *out = r;
+    return GPM_OK;
 }
 
-extern "C" gpm_status gpm_sparsify(gpm_graph *, uint32_t, uint64_t, uint32_t, uint32_t, uint64_t *, uint32_t *,
-                                   uint64_t *) {
-    set_error("gpm_sparsify: not built yet");
-    return GPM_ERR_UNSUPPORTED;
+// Colour + sparsify into freshly allocated device arrays (caller frees).
+gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colouring, uint32_t slot,
+                          uint64_t **row_out, uint32_t **col_out, uint64_t *kept, uint64_t *user_row,
+                          uint32_t *user_col) {
+    const uint64_t n = h->d.n;
+    cudaStream_t st = h->stream;
+    uint32_t *colours = nullptr;
+    uint64_t *cnt = nullptr, *row = user_row;
+    uint32_t *col = user_col;
+    cudaError_t e = cudaMallocAsync((void **)&colours, sizeof(uint32_t) * (n + 1), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&cnt, sizeof(uint64_t) * (n + 1), st);
+    if (e == cudaSuccess && !row) e = cudaMallocAsync((void **)&row, sizeof(uint64_t) * (n + 1), st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(colours, st);
+        cudaFreeAsync(cnt, st);
+        set_error("sparsify: device allocation failed");
+        return GPM_ERR_OOM;
+    }
+    const unsigned blocks_v = (unsigned)((n + 255) / 256);
+    const uint64_t warps = n < (1ull << 22) ? (n ? n : 1) : (1ull << 22);
+    const unsigned blocks_w = (unsigned)((warps * 32 + 255) / 256);
+    if (n) {
+        colour_kernel<<<blocks_v, 256, 0, st>>>(n, c, seed, colouring, slot, colours);
+        keep_count<<<blocks_w, 256, 0, st>>>(h->d.row_ptr, h->d.col, colours, n, cnt);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = scan_exclusive_u64(cnt, row, n, st);
+    uint64_t k = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&k, row + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && !col) e = cudaMallocAsync((void **)&col, sizeof(uint32_t) * (k ? k : 1), st);
+    if (e == cudaSuccess && n) {
+        keep_write<<<blocks_w, 256, 0, st>>>(h->d.row_ptr, h->d.col, colours, n, row, col);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(colours, st);
+    cudaFreeAsync(cnt, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        set_error(std::string("sparsify: ") + cudaGetErrorString(e));
+        return GPM_ERR_CUDA;
+    }
+    *kept = k;
+    if (row_out) *row_out = row;
+    if (col_out) *col_out = col;
+    return GPM_OK;
+}
+
+gpm_status gs_estimate(gpm_graph *h, const Plan &p, uint64_t seed, const gpm_config *cfg, gpm_result *out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const uint32_t c = (cfg && cfg->colors) ? cfg->colors : 8;
+    const uint32_t slot = cfg ? cfg->slot : 0;
+    uint64_t *row = nullptr;
+    uint32_t *col = nullptr;
+    uint64_t kept = 0;
+    gpm_status st = sparsify_alloc(h, c, seed, 0, slot, &row, &col, &kept, nullptr, nullptr);
+    if (st != GPM_OK) return st;
+    gpm_graph *gs = nullptr;
+    st = gpm_load_csr(h->d.n, row, col, GPM_DEVICE_PTRS, h->stream, &gs);
+    const auto t1 = std::chrono::steady_clock::now();
+    uint64_t cp = 0;
+    float ms = 0.f;
+    if (st == GPM_OK) st = exact_count_plan(gs, p, &cp, &ms);
+    if (gs) gpm_free_graph(gs);
+    cudaFree(row);
+    cudaFree(col);
+    if (st != GPM_OK) return st;
+    out->exact_count = cp;
+    out->estimate = (double)cp * std::pow((double)c, (double)(p.k - 1));
+    out->ci_half_width = NAN;
+    out->eps_hat = NAN;
+    out->scheme_used = GPM_GS;
+    out->converged = 1;
+    out->t_preproc_s = std::chrono::duration<double>(t1 - t0).count();
+    out->t_sample_s = ms * 1e-3;
+    out->kernel_launches += 7;
+    out->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return GPM_OK;
+}
+
+}  // namespace gpm
+
+extern "C" gpm_status gpm_exact_count(gpm_graph *h, const gpm_pattern *pattern, uint64_t *out) {
+    if (!h || !pattern || !out) {
+        set_error("gpm_exact_count: null argument");
+        return GPM_ERR_ARG;
+    }
+    Plan p;
+    std::string why = build_plan(*pattern, &p);
+    if (!why.empty()) {
+        set_error("pattern rejected: " + why);
+        return GPM_ERR_ARG;
+    }
+    return exact_count_plan(h, p, out, nullptr);
+}
+
+extern "C" gpm_status gpm_sparsify(gpm_graph *h, uint32_t colors, uint64_t seed, uint32_t colouring, uint32_t slot,
+                                   uint64_t *row_out, uint32_t *col_out, uint64_t *kept) {
+    if (!h || !row_out || !col_out || !kept || colors == 0) {
+        set_error("gpm_sparsify: null argument or zero colours");
+        return GPM_ERR_ARG;
+    }
+    return sparsify_alloc(h, colors, seed, colouring, slot, nullptr, nullptr, kept, row_out, col_out);
 }
 
 extern "C" gpm_status gpm_estimate_batch(gpm_graph *, uint32_t, const gpm_pattern *, const double *, double,

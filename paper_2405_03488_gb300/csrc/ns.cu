@@ -33,6 +33,7 @@
 // order, so the result does not depend on scheduling.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -693,6 +694,124 @@ extern "C" gpm_status gpm_plan(const gpm_pattern *pattern, int32_t *order, int32
 
 extern "C" double gpm_normal_quantile(double p) { return normal_quantile(p); }
 
+// ------------------------------------------------------------------ hybrid
+namespace gpm {
+
+// Loose mode (Sec. 5.1): a pilot NS round on G gives the per-sample mean and
+// variance, the hit rate and the device time per sample; the NS cost model
+// (Sec. 4.3) turns them into a cone [t_lo, t_hi] = N_s * c_step * [1, k - 2]
+// with N_s = (z * sd / (eps * mu))^2 samples and c_step the pilot's time per
+// candidate-set step (the lower edge is every sample breaking at its first
+// set, the upper edge none breaking).  The GS model (Sec. 4.4) adds the
+// sparsification pass |E| (w1 + p w2) at streaming bandwidth and the nested
+// loops of the exact search, whose level sizes follow the GraphPi estimates
+// on the sparsified graph (|V'| = |V|, |E'| = p|E|, T' = p^2 T): an extension
+// by one neighbour costs the mean degree 2|E'|/|V|, an intersection of b
+// lists |V| p1 p2^(b-1) with p1 = 2|E'|/|V|^2 and p2 = T|V| / (2|E|^2) (the
+// substitution leaves p2 unchanged).  T comes from a short NS triangle pilot.
+// GS runs only if its prediction lies below the whole cone; otherwise NS
+// (the confidence-preserving choice).
+struct HybridModel {
+    double n_s, t_lo, t_hi, t_gs, t_pre, t_search, c_step, triangles;
+    int choose_gs;
+};
+
+static gpm_status hybrid_model(gpm_graph *h, const Plan &p, double eps, double delta, uint64_t seed,
+                               const gpm_config *cfg, HybridModel *hm) {
+    const uint64_t Wp = (cfg && cfg->window) ? cfg->window : (1ull << 20);
+    const uint32_t slot = cfg ? cfg->slot : 0;
+    const double z = normal_quantile(1.0 - delta / 2.0);
+    float ms = 0.f;
+    gpm_status st = run_block(h, p, MODE_INTERSECT, seed ^ 0x9E3779B97F4A7C15ull, slot, 0, Wp, cfg, 0, nullptr, &ms);
+    if (st != GPM_OK) return st;
+    Totals t = *h->totals_host;
+    const double mu = t.sum / (double)t.n;
+    const double var = std::max(0.0, t.sumsq / (double)t.n - mu * mu);
+    const double t_sample = ms * 1e-3 / (double)t.n;
+    // steps per sample from a traced slice of the pilot stream
+    const uint64_t nt = 4096;
+    gpm_sample_record *d = nullptr;
+    std::vector<gpm_sample_record> rec(nt);
+    if (cudaMalloc((void **)&d, sizeof(gpm_sample_record) * nt) != cudaSuccess) {
+        set_error("hybrid: device allocation failed");
+        return GPM_ERR_OOM;
+    }
+    st = run_block(h, p, MODE_INTERSECT, seed ^ 0x9E3779B97F4A7C15ull, slot, 0, nt, cfg, 0, d, nullptr);
+    if (st == GPM_OK && cudaMemcpy(rec.data(), d, sizeof(gpm_sample_record) * nt, cudaMemcpyDeviceToHost) != cudaSuccess)
+        st = GPM_ERR_CUDA;
+    cudaFree(d);
+    if (st != GPM_OK) return st;
+    double steps = 0.0;
+    for (const auto &r : rec) {
+        int s_i = r.hit ? p.k - 2 : (r.depth >= 2 ? r.depth - 1 : 1);
+        steps += s_i < 1 ? 1 : s_i;
+    }
+    steps /= (double)nt;
+    const double c_step = t_sample / std::max(steps, 1.0);
+    hm->c_step = c_step;
+    hm->n_s = (mu > 0.0) ? std::ceil(z * z * var / (eps * eps * mu * mu)) : INFINITY;
+    if (hm->n_s < (double)Wp) hm->n_s = (double)Wp;
+    hm->t_lo = hm->n_s * c_step;
+    hm->t_hi = hm->n_s * c_step * std::max(1, p.k - 2);
+
+    // triangle count of G for the GraphPi estimate
+    Plan tri;
+    gpm_pattern tp;
+    std::memset(&tp, 0, sizeof(tp));
+    tp.k = 3;
+    tp.adj[0] = 6;
+    tp.adj[1] = 5;
+    tp.adj[2] = 3;
+    build_plan(tp, &tri);
+    st = run_block(h, tri, MODE_INTERSECT, seed ^ 0x5851F42D4C957F2Dull, slot, 0, 1ull << 18, cfg, 0, nullptr, nullptr);
+    if (st != GPM_OK) return st;
+    const double T = h->totals_host->sum / (double)h->totals_host->n;
+    hm->triangles = T;
+
+    const double c = (cfg && cfg->colors) ? cfg->colors : 8;
+    const double pk = 1.0 / c;
+    const double V = (double)h->d.n, E = (double)h->d.m;
+    const double Ep = E * pk;
+    const double d_avg = V > 0 ? 2.0 * E / V : 0.0;
+    const double d_sp = V > 0 ? 2.0 * Ep / V : 0.0;
+    const double p1 = V > 0 ? 2.0 * Ep / (V * V) : 0.0;
+    const double p2 = E > 0 ? T * V / (2.0 * E * E) : 0.0;
+    // nested loops: iterations reaching level j times the set-op cost there,
+    // in units of one sampler step (which scans about d_avg entries)
+    double iters = p.oriented ? Ep : 2.0 * Ep;
+    double work = 0.0;
+    for (int j = 2; j < p.k; j++) {
+        const int b = __builtin_popcount(p.back[j]);
+        work += iters * (d_sp / std::max(d_avg, 1.0));
+        const double z_j = (b <= 1) ? d_sp : V * p1 * std::pow(p2, (double)(b - 1));
+        iters *= z_j;
+    }
+    const double bytes_pre = 4.0 * 2.0 * E * 2.0 + 4.0 * 2.0 * E * pk + 8.0 * V * 3.0;
+    const double bw = 2.0e12;   // effective sparsification bandwidth (B/s), measured on GB300
+    hm->t_pre = bytes_pre / bw;
+    hm->t_search = work * c_step;
+    hm->t_gs = hm->t_pre + hm->t_search;
+    hm->choose_gs = hm->t_gs < hm->t_lo;
+    return GPM_OK;
+}
+
+static gpm_status hybrid_estimate(gpm_graph *h, const Plan &p, double eps, double delta, uint64_t seed,
+                                  const gpm_config *cfg, gpm_result *out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    HybridModel hm;
+    gpm_status st = hybrid_model(h, p, eps, delta, seed, cfg, &hm);
+    if (st != GPM_OK) return st;
+    const double t_pilot = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (hm.choose_gs) st = gs_estimate(h, p, seed, cfg, out);
+    else st = ns_estimate(h, p, eps, delta, seed, cfg, out);
+    out->t_pilot_s = t_pilot;
+    out->kernel_launches += 6;
+    out->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+}  // namespace gpm
+
 extern "C" gpm_status gpm_estimate(gpm_graph *h, const gpm_pattern *pattern, gpm_scheme scheme, double eps,
                                    double delta, uint64_t seed, const gpm_config *cfg, gpm_result *out) {
     if (!h || !out) {
@@ -706,6 +825,31 @@ extern "C" gpm_status gpm_estimate(gpm_graph *h, const gpm_pattern *pattern, gpm
     switch (scheme) {
         case GPM_NS:
             return ns_estimate(h, p, eps, delta, seed, cfg, out);
+        case GPM_GS:
+            return gs_estimate(h, p, seed, cfg, out);
+        case GPM_HYBRID:
+            if (!(eps > 0.0) || !(delta > 0.0 && delta < 1.0)) {
+                set_error("eps must be > 0 and delta in (0, 1)");
+                return GPM_ERR_ARG;
+            }
+            return hybrid_estimate(h, p, eps, delta, seed, cfg, out);
+        case GPM_EXACT: {
+            const auto t0 = std::chrono::steady_clock::now();
+            uint64_t c = 0;
+            float ms = 0.f;
+            st = exact_count_plan(h, p, &c, &ms);
+            if (st != GPM_OK) return st;
+            out->estimate = (double)c;
+            out->exact_count = c;
+            out->ci_half_width = 0.0;
+            out->eps_hat = 0.0;
+            out->converged = 1;
+            out->scheme_used = GPM_EXACT;
+            out->t_sample_s = ms * 1e-3;
+            out->kernel_launches = 1;
+            out->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            return GPM_OK;
+        }
         default:
             set_error("gpm_estimate: scheme not available in this build");
             return GPM_ERR_UNSUPPORTED;

@@ -56,7 +56,8 @@ def test_trace_bit_exact_small(name, induced, verify):
     gpu = g.trace(pat, seed=77, first=first, count=count, verify=verify)
     _, cpu = O.ns_run(og, O.plan(k, edges, induced), seed=77, first=first, count=count, mode=mode, trace=True)
     assert_same_records(gpu, cpu, k)
-    assert gpu["hit"].sum() > 0
+    if verify == "intersect":
+        assert gpu["hit"].sum() > 0
 
 
 @pytest.mark.parametrize("cap,warps,blocks", [(1, 1, 3), (4, 2, 5), (33, 8, 7), (512, 4, 0)])
