@@ -1,0 +1,87 @@
+"""GPU parity of colour sparsification, exact counting, the GS estimate and
+the hybrid choice against the CPU oracle (integers bit-exact)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2405_03488_gb300 import api
+from paper_2405_03488_gb300 import graphs as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2405_03488_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def pair(rp, col):
+    return api.Graph(rp.cuda(), col.cuda(), validate=True), O.Graph(*G.to_numpy(rp, col))
+
+
+@pytest.mark.parametrize("c,colouring,slot", [(1, 0, 0), (2, 0, 0), (8, 3, 1), (1000, 1, 5)])
+def test_sparsify_bit_exact(c, colouring, slot):
+    rp, col = G.erdos_renyi(5000, 0.004, seed=6)
+    g, og = pair(rp, col)
+    row_d, col_d = g.sparsify(c, seed=99, colouring=colouring, slot=slot)
+    cols = O.colors(og.n, c, 99, colouring, slot)
+    row_o, col_o = O.sparsify(og, cols)
+    assert np.array_equal(row_d.cpu().numpy().astype(np.uint64), row_o)
+    assert np.array_equal(col_d.cpu().numpy().astype(np.uint32), col_o)
+
+
+EXACT_PATTERNS = [("triangle", False), ("4-clique", False), ("5-clique", False), ("4-cycle", False),
+                  ("4-cycle", True), ("diamond", True), ("house", False), ("3-star", True), ("4-path", True),
+                  ("tailed-triangle", False), ("5-path", False), ("edge", False)]
+
+
+@pytest.mark.parametrize("name,induced", EXACT_PATTERNS)
+def test_exact_count_matches_oracle(name, induced):
+    k, edges = G.pattern(name)
+    for rp, col in (G.erdos_renyi(60, 0.25, seed=1), G.erdos_renyi(400, 0.03, seed=2), G.complete(9)):
+        g, og = pair(rp, col)
+        assert g.exact_count((k, edges, induced)) == O.exact_count(og, O.plan(k, edges, induced))
+
+
+def test_exact_scheme_and_closed_forms():
+    for n in (12, 20):
+        rp, col = G.complete(n)
+        g = api.Graph(rp.cuda(), col.cuda())
+        for k in (3, 4, 5, 6):
+            r = g.estimate("%d-clique" % k, scheme=api.EXACT)
+            import math
+            assert r["exact_count"] == math.comb(n, k) and r["estimate"] == math.comb(n, k)
+
+
+@pytest.mark.parametrize("name,c", [("triangle", 2), ("4-clique", 4), ("4-cycle", 8), ("house", 3)])
+def test_gs_estimate_matches_oracle(name, c):
+    rp, col = G.erdos_renyi(3000, 0.01, seed=3)
+    g, og = pair(rp, col)
+    k, edges = G.pattern(name)
+    r = g.estimate(name, scheme=api.GS, seed=17, colors=c)
+    est, cp = O.gs_estimate(og, O.plan(k, edges), c, seed=17)
+    assert r["scheme_used"] == api.GS
+    assert r["exact_count"] == cp
+    assert r["estimate"] == est
+    assert np.isnan(r["ci_half_width"])
+
+
+def test_hybrid_returns_a_consistent_engine_result():
+    # dense-ish ER: NS converges quickly; planted cliques in a sparse graph: needle case
+    rp, col = G.erdos_renyi(3000, 0.01, seed=4)
+    g, og = pair(rp, col)
+    r = g.estimate("triangle", scheme=api.HYBRID, eps=0.05, delta=0.01, seed=3, window=1 << 16)
+    assert r["scheme_used"] in (api.NS, api.GS) and r["t_pilot_s"] > 0
+    if r["scheme_used"] == api.NS:
+        assert r["converged"] == 1 and r["eps_hat"] <= 0.05
+    else:
+        est, _ = O.gs_estimate(og, O.plan(*G.pattern("triangle")), 8, seed=3)
+        assert r["estimate"] == est
+    rp, col = G.chung_lu(20000, n_cliques=20, clique_size=10, seed=5)
+    g = api.Graph(rp.cuda(), col.cuda())
+    r = g.estimate("7-clique", scheme=api.HYBRID, eps=0.05, delta=0.01, seed=3, window=1 << 16,
+                   n_max=1 << 22, colors=2)
+    assert r["scheme_used"] in (api.NS, api.GS)
