@@ -169,6 +169,26 @@ gpm_status gpm_estimate_batch(gpm_graph *g, uint32_t count, const gpm_pattern *p
 gpm_status gpm_sample_sums(gpm_graph *g, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
                            uint64_t count, const gpm_config *cfg, gpm_sums *out);
 
+/* Same result as gpm_sample_sums, for callers that must not allocate device
+ * memory during the call.  The paper has no counterpart: this is a library
+ * convenience.  It is meant for code that records work into a CUDA graph by
+ * stream capture (where the implicit device synchronisation of cudaMalloc is
+ * not allowed), for applications whose own memory pool has already reserved
+ * the device memory, and for latency-bound loops that cannot afford an
+ * allocation's synchronisation.  Instead of handle-owned buffers it keeps its
+ * scratch (per-chunk partials, chunk counter, totals) in one fixed array of
+ * about 2 MiB that every GPU loading the library holds until the process
+ * exits.  Limits and rules:
+ *  - count <= 2^26 samples per call, else GPM_ERR_ARG (nothing launched);
+ *  - the handle must come from gpm_load_csr (which allocates once, up front);
+ *  - the first call on a device looks up the array's device address, so make
+ *    that first call before any stream capture begins;
+ *  - all calls in the process share the one array and leave their contents in
+ *    it: calls whose work overlaps on the GPU (other streams, other threads)
+ *    race and must be serialised by the caller. */
+gpm_status gpm_sample_sums_static(gpm_graph *g, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
+                                  uint64_t count, const gpm_config *cfg, gpm_sums *out);
+
 /* Per-sample records of samples [first, first + count) into HOST memory. */
 gpm_status gpm_trace(gpm_graph *g, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
                      uint64_t count, const gpm_config *cfg, gpm_sample_record *out);

@@ -77,6 +77,7 @@ SIGNATURES = [
     ("gpm_estimate", _i32, [_V, P(Pattern), _i32, _dbl, _dbl, _u64, P(Config), P(Result)]),
     ("gpm_estimate_batch", _i32, [_V, _u32, P(Pattern), P(_dbl), _dbl, _u64, P(Config), P(Result)]),
     ("gpm_sample_sums", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), P(Sums)]),
+    ("gpm_sample_sums_static", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), P(Sums)]),
     ("gpm_trace", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), _V]),
     ("gpm_exact_count", _i32, [_V, P(Pattern), P(_u64)]),
     ("gpm_sparsify", _i32, [_V, _u32, _u64, _u32, _u32, _V, _V, P(_u64)]),

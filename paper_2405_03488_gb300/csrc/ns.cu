@@ -37,6 +37,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "device.cuh"
@@ -854,4 +855,107 @@ extern "C" gpm_status gpm_estimate(gpm_graph *h, const gpm_pattern *pattern, gpm
             set_error("gpm_estimate: scheme not available in this build");
             return GPM_ERR_UNSUPPORTED;
     }
+}
+
+// ------------------------------------------------------------------ static-scratch variant
+// gpm_sample_sums_static: the same sampler and chunk-order reduction as
+// gpm_sample_sums, with every scratch word (per-chunk partials, the chunk
+// counter, the totals) in one file-scope device array instead of memory the
+// handle allocates, so the call itself allocates no device or pinned memory.
+namespace gpm {
+
+constexpr uint32_t kStaticMaxChunks = 1u << 16;          // partials per call
+constexpr uint64_t kStaticMaxSamples = 1ull << 26;       // samples per call
+constexpr size_t kStaticPartialBytes = sizeof(Partial) * kStaticMaxChunks;
+constexpr size_t kStaticScratchBytes = kStaticPartialBytes + 256 + 256;   // partials | totals | counter
+
+// About 2 MiB; every GPU that loads the library holds it until the process exits.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+static std::mutex g_static_mu;
+static void *g_static_addr[256];
+
+// Device address of g_static_scratch for the current device, looked up once
+// per device (the array's name in host code is only a host-side stand-in).
+static gpm_status static_scratch_addr(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 256) {
+        set_error("gpm_sample_sums_static: no current CUDA device");
+        return GPM_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error(std::string("gpm_sample_sums_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            return GPM_ERR_CUDA;
+        }
+        g_static_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_static_addr[dev]);
+    return GPM_OK;
+}
+
+}  // namespace gpm
+
+extern "C" gpm_status gpm_sample_sums_static(gpm_graph *h, const gpm_pattern *pattern, uint64_t seed,
+                                             uint64_t first, uint64_t count, const gpm_config *cfg,
+                                             gpm_sums *out) {
+    if (!h || !out) {
+        set_error("gpm_sample_sums_static: null argument");
+        return GPM_ERR_ARG;
+    }
+    if (count > kStaticMaxSamples) {
+        set_error("gpm_sample_sums_static: count exceeds the static scratch limit of 2^26 samples per call");
+        return GPM_ERR_ARG;
+    }
+    Plan p;
+    gpm_status st = plan_or_error(pattern, &p);
+    if (st != GPM_OK) return st;
+    std::memset(out, 0, sizeof(*out));
+    if (count == 0) return GPM_OK;
+    unsigned char *base = nullptr;
+    st = static_scratch_addr(&base);
+    if (st != GPM_OK) return st;
+    Partial *parts = reinterpret_cast<Partial *>(base);
+    Totals *tot = reinterpret_cast<Totals *>(base + kStaticPartialBytes);
+    unsigned int *ctr = reinterpret_cast<unsigned int *>(base + kStaticPartialBytes + 256);
+
+    Shape sh = pick_shape(h, cfg, count);
+    const uint64_t min_chunk = (count + kStaticMaxChunks - 1) / kStaticMaxChunks;
+    if (sh.chunk < min_chunk) sh.chunk = (uint32_t)min_chunk;
+    const uint64_t nchunks = (count + sh.chunk - 1) / sh.chunk;
+    RunArgs a;
+    a.seed = seed;
+    a.first = first;
+    a.count = count;
+    a.partials = parts;
+    a.counter = ctr;
+    a.trace = nullptr;
+    a.slot = cfg ? cfg->slot : 0;
+    a.cap = sh.cap;
+    a.chunk = sh.chunk;
+    a.nchunks = (uint32_t)nchunks;
+    cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(unsigned int), h->stream);
+    if (e == cudaSuccess)
+        e = (mode_of(cfg) == MODE_CHECK) ? launch_ns<MODE_CHECK, false>(h, p, sh, a)
+                                         : launch_ns<MODE_INTERSECT, false>(h, p, sh, a);
+    if (e == cudaSuccess) {
+        reduce_partials<<<1, 1024, 0, h->stream>>>(parts, (uint32_t)nchunks, tot, 0);
+        e = cudaGetLastError();
+    }
+    Totals t;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&t, tot, sizeof(Totals), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("gpm_sample_sums_static: ") + cudaGetErrorString(e));
+        return GPM_ERR_CUDA;
+    }
+    out->n = t.n;
+    out->hits = t.hits;
+    out->sum = t.sum;
+    out->sumsq = t.sumsq;
+    return GPM_OK;
 }
