@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="gpm", choices=["gpm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ncu-case", default=None, choices=["4-clique", "5-clique"],
+                    help="profiling case: R-MAT 22 resident, --steps sampler launches of one window each")
     return ap.parse_args()
 
 
@@ -222,10 +224,31 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def ncu_case(args):
+    """A small, self-contained case for ncu: the graph stays resident, the
+    generator's temporaries are released, and --steps launches of one window
+    (2^20 samples) of the sampler run after --warmup untimed ones."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_03488_gb300 import api
+    rp, col = make_graph("cuda")
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    g = api.Graph(rp, col)
+    for s in range(args.warmup + args.steps):
+        g.sample_sums(args.ncu_case, seed=1 + s, first=0, count=WINDOW)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": args.ncu_case, "launches": args.warmup + args.steps, "window": WINDOW}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.ncu_case:
+        ncu_case(args)
         return
     rank, world, local = dist_env()
     import numpy as np

@@ -158,11 +158,22 @@ gpm_status gpm_graph_info(const gpm_graph *g, uint64_t *n, uint64_t *m, uint64_t
 gpm_status gpm_estimate(gpm_graph *g, const gpm_pattern *pattern, gpm_scheme scheme, double eps,
                         double delta, uint64_t seed, const gpm_config *cfg, gpm_result *out);
 
-/* Many (pattern, eps) jobs in one persistent launch per round; job i uses
- * RNG slot i.  out has count entries. */
+/* Many (pattern, eps) jobs at once: every round is one persistent sampler
+ * launch over the chunks of all jobs still running, followed by a per-job
+ * reduction and convergence test on the device; rounds run as a captured CUDA
+ * graph.  Job i uses RNG slot cfg->slot + i, so its result equals a separate
+ * gpm_estimate with that slot.  out has count entries; at most 1024 jobs.
+ * GPM_ERR_NOT_CONVERGED if any job hit n_max (all results filled). */
 gpm_status gpm_estimate_batch(gpm_graph *g, uint32_t count, const gpm_pattern *patterns,
                               const double *eps, double delta, uint64_t seed, const gpm_config *cfg,
                               gpm_result *out);
+
+/* Times one convergence round of the batch under each candidate launch shape
+ * (2, 4 or 8 warps per block; on-chip candidate buffers of 256, 512 or 1024
+ * entries per warp) and writes the fastest into io->block_warps and io->cap.
+ * Estimates do not depend on the shape: samples are grouped in fixed chunks of
+ * 64 whose partials are reduced in chunk order. */
+gpm_status gpm_autotune(gpm_graph *g, uint32_t count, const gpm_pattern *patterns, uint64_t seed, gpm_config *io);
 
 /* Samples [first, first + count) of an NS run (Algorithm 3's inner loop):
  * totals of X_i and X_i^2 in FP64.  cfg selects verify mode, slot and MLP. */

@@ -76,6 +76,7 @@ SIGNATURES = [
     ("gpm_graph_info", _i32, [_V, P(_u64), P(_u64), P(_u64), P(_u64)]),
     ("gpm_estimate", _i32, [_V, P(Pattern), _i32, _dbl, _dbl, _u64, P(Config), P(Result)]),
     ("gpm_estimate_batch", _i32, [_V, _u32, P(Pattern), P(_dbl), _dbl, _u64, P(Config), P(Result)]),
+    ("gpm_autotune", _i32, [_V, _u32, P(Pattern), _u64, P(Config)]),
     ("gpm_sample_sums", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), P(Sums)]),
     ("gpm_sample_sums_static", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), P(Sums)]),
     ("gpm_trace", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), _V]),

@@ -116,6 +116,13 @@ class Graph:
         check(code, "gpm_estimate_batch", (_lib.GPM_OK, _lib.GPM_ERR_NOT_CONVERGED))
         return [r.as_dict() for r in res]
 
+    def autotune(self, pats, seed=1, **cfg):
+        """Fastest launch shape for these patterns: dict(block_warps, cap)."""
+        arr = (_lib.Pattern * len(pats))(*[pattern(p) for p in pats])
+        c = config(**cfg)
+        check(_lib.load().gpm_autotune(self.h, len(pats), arr, seed, C.byref(c)), "gpm_autotune")
+        return {"block_warps": c.block_warps, "cap": c.cap}
+
     def sample_sums(self, pat, seed, first, count, **cfg):
         out = _lib.Sums()
         pp = pattern(pat)

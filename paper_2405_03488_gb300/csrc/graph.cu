@@ -146,6 +146,20 @@ __global__ void upper_index(const uint64_t *__restrict__ row_ptr, const uint32_t
     cnt[v] = end - lo;
 }
 
+// Oriented edge e (canonical order: u ascending, then N+(u) ascending) stored
+// as (w << 32 | u), so a sample reads its first edge with one 8-byte load.
+__global__ void oriented_edges(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
+                               const uint64_t *__restrict__ up, const uint64_t *__restrict__ uoff, uint64_t n,
+                               uint64_t *edges) {
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const unsigned lane = threadIdx.x & 31u;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t u = warp; u < n; u += nw) {
+        const uint64_t b = up[u], e = row_ptr[u + 1], o = uoff[u];
+        for (uint64_t i = b + lane; i < e; i += 32) edges[o + (i - b)] = ((uint64_t)col[i] << 32) | u;
+    }
+}
+
 __global__ void max_degree_kernel(const uint64_t *__restrict__ row_ptr, uint64_t n, unsigned long long *out) {
     uint64_t best = 0;
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
@@ -327,6 +341,23 @@ extern "C" gpm_status gpm_load_csr(uint64_t n, const uint64_t *row_ptr, const ui
     g->d.uoff = g->uoff;
     g->d.m = m;
     g->max_degree = maxd_h;
+    // optional first-edge table; without memory for it the sampler searches uoff
+    g->d.edges = nullptr;
+    if (m > 0 && cudaMalloc((void **)&g->edges, sizeof(uint64_t) * m) == cudaSuccess) {
+        const uint64_t warps = n < (1ull << 22) ? n : (1ull << 22);
+        oriented_edges<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(g->d.row_ptr, g->d.col, g->up, g->uoff,
+                                                                             n, g->edges);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error(std::string("gpm_load_csr: edge table: ") + cudaGetErrorString(e));
+            return fail(GPM_ERR_CUDA);
+        }
+        g->d.edges = g->edges;
+    } else {
+        g->edges = nullptr;
+        cudaGetLastError();
+    }
     *out = g;
     return GPM_OK;
 }
@@ -339,6 +370,7 @@ extern "C" void gpm_free_graph(gpm_graph *g) {
     cudaFree(g->own_col);
     cudaFree(g->up);
     cudaFree(g->uoff);
+    cudaFree(g->edges);
     cudaFree(g->partials);
     cudaFree(g->totals);
     cudaFree(g->counter);

@@ -148,7 +148,11 @@ __global__ void __launch_bounds__(256) exact_kernel(const DGraph g, const Plan p
         const uint64_t e1 = (e0 + per_grab < M) ? e0 + per_grab : M;
         for (uint64_t e = e0; e < e1; e++) {
             uint32_t v0, v1;
-            if (p.oriented) {
+            if (p.oriented && g.edges) {
+                const uint64_t pr = __ldg(g.edges + e);
+                v0 = (uint32_t)pr;
+                v1 = (uint32_t)(pr >> 32);
+            } else if (p.oriented) {
                 const uint64_t u = warp_upper_bound(g.uoff, g.n + 1, e) - 1;
                 v0 = (uint32_t)u;
                 v1 = __ldg(g.col + __ldg(g.up + u) + (e - __ldg(g.uoff + u)));
@@ -362,10 +366,4 @@ extern "C" gpm_status gpm_sparsify(gpm_graph *h, uint32_t colors, uint64_t seed,
         return GPM_ERR_ARG;
     }
     return sparsify_alloc(h, colors, seed, colouring, slot, nullptr, nullptr, kept, row_out, col_out);
-}
-
-extern "C" gpm_status gpm_estimate_batch(gpm_graph *, uint32_t, const gpm_pattern *, const double *, double,
-                                         uint64_t, const gpm_config *, gpm_result *) {
-    set_error("gpm_estimate_batch: not built yet");
-    return GPM_ERR_UNSUPPORTED;
 }

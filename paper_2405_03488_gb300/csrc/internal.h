@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/gpm.h"
 
@@ -34,6 +35,7 @@ struct DGraph {
     const uint32_t *col;       // nnz
     const uint64_t *up;        // n: index of the first neighbour above v
     const uint64_t *uoff;      // n + 1: prefix sum of |N+(u)|
+    const uint64_t *edges;     // m oriented edges (w << 32 | u), u < w, or null
     uint64_t n, nnz, m;
 };
 
@@ -61,6 +63,8 @@ gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colo
                           uint64_t **row_out, uint32_t **col_out, uint64_t *kept, uint64_t *user_row,
                           uint32_t *user_col);
 double normal_quantile(double p);
+gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const double *eps, double delta,
+                          uint64_t seed, const gpm_config *cfg, gpm_result *results);
 }  // namespace gpm
 
 // The opaque handle.
@@ -72,6 +76,7 @@ struct gpm_graph {
     uint64_t *own_row_ptr;
     uint32_t *own_col;
     uint64_t *up, *uoff;
+    uint64_t *edges;              // materialised oriented edges (optional)
     // sampler scratch
     gpm::Partial *partials;
     uint64_t partials_cap;

@@ -42,266 +42,12 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "sampler.cuh"
 
 namespace gpm {
 
-enum { MODE_INTERSECT = 0, MODE_CHECK = 1 };
-
-struct RunArgs {
-    uint64_t seed;
-    uint64_t first;               // first sample index of this launch
-    uint64_t count;               // samples in this launch
-    Partial *partials;            // one per chunk
-    unsigned int *counter;        // chunk dispenser
-    gpm_sample_record *trace;     // optional per-sample records (device)
-    uint32_t slot;
-    uint32_t cap;                 // entries per on-chip candidate buffer
-    uint32_t chunk;               // samples per chunk
-    uint32_t nchunks;
-};
-
-constexpr int kWarpHeaderWords = 40;   // 12 u64 factors + 16 u32 vertices
-
-struct WarpMem {
-    uint64_t *fac;
-    uint32_t *v;
-    uint32_t *S0, *S1;
-};
-
-__device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        uint64_t t = __shfl_xor_sync(kFull, x, o);
-        x = t < x ? t : x;
-    }
-    return x;
-}
-
-__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
-
-// Conditions of S_j other than membership in the driver list.
-__device__ __forceinline__ bool cand_ok(const DGraph &g, const Plan &p, const uint32_t *v, int j, int driver,
-                                        uint64_t lb, uint64_t le, uint32_t x) {
-    bool ok = true;
-    const uint32_t back = p.back[j];
-    for (int i = 0; i < j; i++) {
-        const uint64_t b = __shfl_sync(kFull, lb, i);
-        const uint64_t e = __shfl_sync(kFull, le, i);
-        ok = ok && (x != v[i]);
-        const bool edge = (back >> i) & 1u;
-        if (edge && i != driver) ok = ok && lane_contains(g.col + b, e - b, x);
-        else if (!edge && p.induced) ok = ok && !lane_contains(g.col + b, e - b, x);
-    }
-    return ok;
-}
-
-// Result of one sample, uniform across the warp.
-struct SampleOut {
-    double w;
-    uint64_t wu;
-    int depth;
-    bool hit, overflow;
-};
-
-template <int MODE>
-__device__ SampleOut sample_one(const DGraph &g, const Plan &p, const RunArgs &a, uint64_t s, WarpMem &wm) {
-    const unsigned lane = lane_id();
-    const int k = p.k;
-    SampleOut out;
-    out.w = 0.0;
-    out.wu = 0;
-    out.depth = 0;
-    out.hit = false;
-    out.overflow = false;
-
-    const int nb = k / 2;  // Philox blocks for the k-1 choices
-    Philox4 o = {0u, 0u, 0u, 0u};
-    if ((int)lane < nb)
-        o = philox10((uint32_t)s, (uint32_t)(s >> 32), lane, a.slot << 8, (uint32_t)a.seed,
-                     (uint32_t)(a.seed >> 32));
-    auto word = [&](int t) -> uint64_t {
-        uint32_t lo = (t & 1) ? o.z : o.x;
-        uint32_t hi = (t & 1) ? o.w : o.y;
-        lo = __shfl_sync(kFull, lo, t >> 1);
-        hi = __shfl_sync(kFull, hi, t >> 1);
-        return ((uint64_t)hi << 32) | lo;
-    };
-
-    const uint64_t M = p.oriented ? g.m : g.nnz;
-    if (lane == 0) wm.fac[0] = M;
-    if (M == 0) return out;
-    const uint64_t e = index_map(word(0), M);
-    uint32_t v0, v1;
-    if (p.oriented) {
-        const uint64_t u = warp_upper_bound(g.uoff, g.n + 1, e) - 1;
-        v0 = (uint32_t)u;
-        v1 = __ldg(g.col + __ldg(g.up + u) + (e - __ldg(g.uoff + u)));
-    } else {
-        const uint64_t u = warp_upper_bound(g.row_ptr, g.n + 1, e) - 1;
-        v0 = (uint32_t)u;
-        v1 = __ldg(g.col + e);
-    }
-    uint64_t lb = 0, le = 0;  // lane i: CSR range of v_i
-    if (lane == 0) {
-        lb = __ldg(g.row_ptr + v0);
-        le = __ldg(g.row_ptr + v0 + 1);
-        wm.v[0] = v0;
-        wm.v[1] = v1;
-    } else if (lane == 1) {
-        lb = __ldg(g.row_ptr + v1);
-        le = __ldg(g.row_ptr + v1 + 1);
-    }
-    __syncwarp();
-    out.depth = 2;
-    double w = (double)M;
-    uint64_t wu = M;
-    bool ovf = false;
-    uint32_t prev_size = 0;
-    bool prev_mat = false;
-
-    for (int j = 2; j < k; j++) {
-        const uint32_t lm = p.lower[j];
-        const bool has_lo = lm != 0;
-        uint32_t lo = 0;
-        for (int i = 0; i < j; i++)
-            if ((lm >> i) & 1u) lo = wm.v[i] > lo ? wm.v[i] : lo;
-        const uint64_t r = word(j - 1);
-        uint64_t size = 0;
-        uint32_t x = 0;
-        if (MODE == MODE_CHECK) {
-            const int pb = (int)p.last_back[j];
-            const uint64_t b = __shfl_sync(kFull, lb, pb);
-            const uint64_t en = __shfl_sync(kFull, le, pb);
-            const uint64_t start = has_lo ? b + warp_upper_bound(g.col + b, en - b, lo) : b;
-            size = en - start;
-            if (lane == 0) wm.fac[j] = size;
-            if (size == 0) {
-                out.depth = j;
-                return out;
-            }
-            x = __ldg(g.col + start + index_map(r, size));
-            bool okl = true;
-            if ((int)lane < j) {
-                okl = (x != wm.v[lane]);
-                const bool edge = (p.back[j] >> lane) & 1u;
-                if (edge) {
-                    if ((int)lane != pb) okl = okl && lane_contains(g.col + lb, le - lb, x);
-                } else if (p.induced) {
-                    okl = okl && !lane_contains(g.col + lb, le - lb, x);
-                }
-            }
-            if (!__all_sync(kFull, okl)) {
-                out.depth = j;
-                return out;
-            }
-        } else {
-            uint32_t *Sc = (j & 1) ? wm.S1 : wm.S0;
-            const uint32_t *Sp = (j & 1) ? wm.S0 : wm.S1;
-            uint64_t count = 0;
-            bool mat;
-            if (p.reuse[j] && prev_mat) {
-                const uint64_t b = __shfl_sync(kFull, lb, j - 1);
-                const uint64_t en = __shfl_sync(kFull, le, j - 1);
-                const uint64_t start = has_lo ? b + warp_upper_bound(g.col + b, en - b, lo) : b;
-                const uint64_t L = en - start;
-                const uint32_t P = prev_size;
-                if (L <= 8ull * P + 32) {
-                    for (uint64_t base = start; base < en; base += 32) {
-                        const uint64_t idx = base + lane;
-                        const bool valid = idx < en;
-                        const uint32_t y = valid ? __ldg(g.col + idx) : 0u;
-                        const bool ok = valid && lane_contains_shared(Sp, P, y);
-                        const unsigned m = __ballot_sync(kFull, ok);
-                        if (ok) Sc[count + __popc(m & lanemask_lt())] = y;
-                        count += __popc(m);
-                    }
-                } else {
-                    for (uint32_t base = 0; base < P; base += 32) {
-                        const uint32_t idx = base + lane;
-                        const bool valid = idx < P;
-                        const uint32_t y = valid ? Sp[idx] : 0u;
-                        const bool ok = valid && (!has_lo || y > lo) && lane_contains(g.col + start, L, y);
-                        const unsigned m = __ballot_sync(kFull, ok);
-                        if (ok) Sc[count + __popc(m & lanemask_lt())] = y;
-                        count += __popc(m);
-                    }
-                }
-                mat = true;
-            } else {
-                const uint32_t back = p.back[j];
-                const uint64_t key =
-                    ((int)lane < j && ((back >> lane) & 1u)) ? (((le - lb) << 5) | lane) : ~0ull;
-                const int driver = (int)(warp_min_u64(key) & 31u);
-                const uint64_t b = __shfl_sync(kFull, lb, driver);
-                const uint64_t en = __shfl_sync(kFull, le, driver);
-                const uint64_t start = has_lo ? b + warp_upper_bound(g.col + b, en - b, lo) : b;
-                for (uint64_t base = start; base < en; base += 32) {
-                    const uint64_t idx = base + lane;
-                    const bool valid = idx < en;
-                    const uint32_t y = valid ? __ldg(g.col + idx) : 0u;
-                    const bool ok = cand_ok(g, p, wm.v, j, driver, lb, le, y) && valid;
-                    const unsigned m = __ballot_sync(kFull, ok);
-                    if (ok) {
-                        const uint64_t pos = count + __popc(m & lanemask_lt());
-                        if (pos < a.cap) Sc[pos] = y;
-                    }
-                    count += __popc(m);
-                }
-                mat = count <= a.cap;
-                if (!mat && count > 0) {
-                    // second pass: locate the drawn element without storing the set
-                    const uint64_t target = index_map(r, count);
-                    uint64_t seen = 0;
-                    for (uint64_t base = start; base < en; base += 32) {
-                        const uint64_t idx = base + lane;
-                        const bool valid = idx < en;
-                        const uint32_t y = valid ? __ldg(g.col + idx) : 0u;
-                        const bool ok = cand_ok(g, p, wm.v, j, driver, lb, le, y) && valid;
-                        const unsigned m = __ballot_sync(kFull, ok);
-                        const uint64_t c = __popc(m);
-                        if (seen + c > target) {
-                            const uint32_t rank = (uint32_t)(target - seen);
-                            const bool mine = ok && (uint32_t)__popc(m & lanemask_lt()) == rank;
-                            const int src = __ffs(__ballot_sync(kFull, mine)) - 1;
-                            x = __shfl_sync(kFull, y, src);
-                            break;
-                        }
-                        seen += c;
-                    }
-                }
-            }
-            size = count;
-            if (lane == 0) wm.fac[j] = size;
-            if (size == 0) {
-                out.depth = j;
-                return out;
-            }
-            __syncwarp();
-            if (mat) x = Sc[index_map(r, size)];
-            prev_size = (uint32_t)(mat ? size : 0);
-            prev_mat = mat;
-        }
-        if (lane == 0) wm.v[j] = x;
-        if ((int)lane == j && j + 1 < k) {
-            lb = __ldg(g.row_ptr + x);
-            le = __ldg(g.row_ptr + x + 1);
-        }
-        __syncwarp();
-        w = __dmul_rn(w, (double)size);
-        if (__umul64hi(wu, size) != 0) ovf = true;
-        wu = wu * size;
-        out.depth = j + 1;
-    }
-    out.hit = true;
-    out.depth = k;
-    out.w = w;
-    out.wu = ovf ? 0 : wu;
-    out.overflow = ovf;
-    return out;
-}
-
 template <int MODE, bool TRACE>
-__global__ void __launch_bounds__(256) ns_kernel(const DGraph g, const Plan p, const RunArgs a) {
+__global__ void __launch_bounds__(256, 4) ns_kernel(const DGraph g, const Plan p, const RunArgs a) {
     extern __shared__ uint64_t smem64[];
     uint32_t *smem = reinterpret_cast<uint32_t *>(smem64);
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
@@ -407,15 +153,6 @@ __global__ void __launch_bounds__(1024) reduce_partials(const Partial *__restric
     }
 }
 
-// ------------------------------------------------------------------ host side
-struct Shape {
-    uint32_t blocks, warps, cap, chunk;
-};
-
-static size_t smem_bytes(const Shape &sh) {
-    return (size_t)sh.warps * (kWarpHeaderWords + 2 * sh.cap) * sizeof(uint32_t);
-}
-
 template <int MODE, bool TRACE>
 static cudaError_t launch_ns(gpm_graph *h, const Plan &p, const Shape &sh, const RunArgs &a) {
     auto kern = ns_kernel<MODE, TRACE>;
@@ -424,22 +161,16 @@ static cudaError_t launch_ns(gpm_graph *h, const Plan &p, const Shape &sh, const
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<sh.blocks, sh.warps * 32, smem, h->stream>>>(h->d, p, a);
+    uint32_t blocks = sh.blocks;
+    if (blocks == 0) {
+        // persistent grid: as many blocks as stay resident on every SM
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)(sh.warps * 32), smem);
+        if (e != cudaSuccess) return e;
+        blocks = (uint32_t)((per_sm > 0 ? per_sm : 1) * h->sm_count);
+    }
+    kern<<<blocks, sh.warps * 32, smem, h->stream>>>(h->d, p, a);
     return cudaGetLastError();
-}
-
-static Shape pick_shape(gpm_graph *h, const gpm_config *cfg, uint64_t count) {
-    Shape sh;
-    sh.warps = (cfg && cfg->block_warps) ? cfg->block_warps : 8;
-    sh.cap = (cfg && cfg->cap) ? cfg->cap : 512;
-    uint32_t per_sm = 6;
-    sh.blocks = (cfg && cfg->grid_blocks) ? cfg->grid_blocks : (uint32_t)h->sm_count * per_sm;
-    const uint64_t warps = (uint64_t)sh.blocks * sh.warps;
-    uint64_t chunk = count / (warps * 4);
-    if (chunk < 1) chunk = 1;
-    if (chunk > 256) chunk = 256;
-    sh.chunk = (uint32_t)chunk;
-    return sh;
 }
 
 static gpm_status ensure_partials(gpm_graph *h, uint64_t n) {
@@ -550,79 +281,17 @@ double normal_quantile(double p) {
     return upper ? -x : x;
 }
 
-// Algorithm 3's end-of-window statistics.
-static void error_of(const Totals &t, double z, double *mu, double *half, double *eps_hat) {
-    const double n = (double)t.n;
-    const double m = t.sum / n;
-    double var = t.sumsq / n - m * m;
-    if (var < 0.0) var = 0.0;
-    const double sigma = std::sqrt(var / n);
-    *mu = m;
-    *half = z * sigma;
-    *eps_hat = (m > 0.0) ? z * sigma / m : INFINITY;
-}
-
+// A single NS estimate is a batch of one job (rounds in a captured CUDA
+// graph, Eq. equ:error evaluated on the device after each round).
 gpm_status ns_estimate(gpm_graph *h, const Plan &p, double eps, double delta, uint64_t seed,
                        const gpm_config *cfg, gpm_result *out) {
-    const auto t0 = std::chrono::steady_clock::now();
-    const uint64_t W = (cfg && cfg->window) ? cfg->window : (1ull << 20);
-    const uint64_t n_min = (cfg && cfg->n_min) ? cfg->n_min : W;
-    const uint64_t n_max = (cfg && cfg->n_max) ? cfg->n_max : (1ull << 40);
-    const double max_s = cfg ? cfg->max_seconds : 0.0;
-    const uint32_t slot = cfg ? cfg->slot : 0;
-    const int mode = mode_of(cfg);
     if (!(eps > 0.0) || !(delta > 0.0 && delta < 1.0)) {
         set_error("eps must be > 0 and delta in (0, 1)");
         return GPM_ERR_ARG;
     }
-    const double z = normal_quantile(1.0 - delta / 2.0);
     h->abort_flag = 0;
-    double t_kernel = 0.0;
-    gpm_status status = GPM_OK;
-    uint64_t rounds = 0;
-    for (;;) {
-        float ms = 0.f;
-        gpm_status st = run_block(h, p, mode, seed, slot, rounds * W, W, cfg, rounds > 0, nullptr, &ms);
-        if (st != GPM_OK) return st;
-        rounds++;
-        t_kernel += ms * 1e-3;
-        out->kernel_launches += 2;
-        const Totals &t = *h->totals_host;
-        double mu, half, eh;
-        error_of(t, z, &mu, &half, &eh);
-        out->estimate = mu;
-        out->ci_half_width = half;
-        out->eps_hat = eh;
-        out->sum = t.sum;
-        out->sumsq = t.sumsq;
-        out->samples = t.n;
-        out->hits = t.hits;
-        out->rounds = rounds;
-        if (t.n >= n_min && mu > 0.0 && eh <= eps) {
-            out->converged = 1;
-            break;
-        }
-        if (t.n >= n_max) {
-            status = GPM_ERR_NOT_CONVERGED;
-            set_error("n_max reached before eps_hat <= eps");
-            break;
-        }
-        if (h->abort_flag) {
-            status = GPM_ERR_ABORTED;
-            set_error("aborted");
-            break;
-        }
-        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (max_s > 0.0 && el >= max_s) {
-            status = GPM_ERR_NOT_CONVERGED;
-            set_error("max_seconds reached before eps_hat <= eps");
-            break;
-        }
-    }
-    out->scheme_used = GPM_NS;
-    out->t_sample_s = t_kernel;
-    out->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    return status;
+    std::vector<Plan> plans(1, p);
+    return batch_estimate(h, plans, &eps, delta, seed, cfg, out);
 }
 
 }  // namespace gpm

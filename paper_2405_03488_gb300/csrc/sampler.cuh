@@ -1,0 +1,387 @@
+// Per-sample device code of the NS sampler, shared by the single-run and the
+// batched kernels.  See ns.cu for the method and the layout.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace gpm {
+
+enum { MODE_INTERSECT = 0, MODE_CHECK = 1 };
+
+struct RunArgs {
+    uint64_t seed;
+    uint64_t first;               // first sample index of this launch
+    uint64_t count;               // samples in this launch
+    Partial *partials;            // one per chunk
+    unsigned int *counter;        // chunk dispenser
+    gpm_sample_record *trace;     // optional per-sample records (device)
+    uint32_t slot;
+    uint32_t cap;                 // entries per on-chip candidate buffer
+    uint32_t chunk;               // samples per chunk
+    uint32_t nchunks;
+};
+
+constexpr int kWarpHeaderWords = 40;   // 12 u64 factors + 16 u32 vertices
+
+struct WarpMem {
+    uint64_t *fac;
+    uint32_t *v;
+    uint32_t *S0, *S1;
+};
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        uint64_t t = __shfl_xor_sync(kFull, x, o);
+        x = t < x ? t : x;
+    }
+    return x;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+// Conditions of S_j other than membership in the driver list.
+__device__ __forceinline__ bool cand_ok(const DGraph &g, const Plan &p, const uint32_t *v, int j, int driver,
+                                        uint64_t lb, uint64_t le, uint32_t x) {
+    bool ok = true;
+    const uint32_t back = p.back[j];
+    for (int i = 0; i < j; i++) {
+        const uint64_t b = __shfl_sync(kFull, lb, i);
+        const uint64_t e = __shfl_sync(kFull, le, i);
+        ok = ok && (x != v[i]);
+        const bool edge = (back >> i) & 1u;
+        if (edge && i != driver) ok = ok && lane_contains(g.col + b, e - b, x);
+        else if (!edge && p.induced) ok = ok && !lane_contains(g.col + b, e - b, x);
+    }
+    return ok;
+}
+
+// Result of one sample, uniform across the warp.
+struct SampleOut {
+    double w;
+    uint64_t wu;
+    int depth;
+    bool hit, overflow;
+};
+
+template <int MODE>
+__device__ SampleOut sample_one(const DGraph &g, const Plan &p, const RunArgs &a, uint64_t s, WarpMem &wm) {
+    const unsigned lane = lane_id();
+    const int k = p.k;
+    SampleOut out;
+    out.w = 0.0;
+    out.wu = 0;
+    out.depth = 0;
+    out.hit = false;
+    out.overflow = false;
+
+    const int nb = k / 2;  // Philox blocks for the k-1 choices
+    Philox4 o = {0u, 0u, 0u, 0u};
+    if ((int)lane < nb)
+        o = philox10((uint32_t)s, (uint32_t)(s >> 32), lane, a.slot << 8, (uint32_t)a.seed,
+                     (uint32_t)(a.seed >> 32));
+    auto word = [&](int t) -> uint64_t {
+        uint32_t lo = (t & 1) ? o.z : o.x;
+        uint32_t hi = (t & 1) ? o.w : o.y;
+        lo = __shfl_sync(kFull, lo, t >> 1);
+        hi = __shfl_sync(kFull, hi, t >> 1);
+        return ((uint64_t)hi << 32) | lo;
+    };
+
+    const uint64_t M = p.oriented ? g.m : g.nnz;
+    if (lane == 0) wm.fac[0] = M;
+    if (M == 0) return out;
+    const uint64_t e = index_map(word(0), M);
+    uint32_t v0, v1;
+    uint64_t pos01 = ~0ull;  // index of v1 inside N(v0) in col, when known
+    if (p.oriented && g.edges) {
+        const uint64_t pr = __ldg(g.edges + e);
+        v0 = (uint32_t)pr;
+        v1 = (uint32_t)(pr >> 32);
+    } else if (p.oriented) {
+        const uint64_t u = warp_upper_bound(g.uoff, g.n + 1, e) - 1;
+        v0 = (uint32_t)u;
+        pos01 = __ldg(g.up + u) + (e - __ldg(g.uoff + u));
+        v1 = __ldg(g.col + pos01);
+    } else {
+        const uint64_t u = warp_upper_bound(g.row_ptr, g.n + 1, e) - 1;
+        v0 = (uint32_t)u;
+        pos01 = e;
+        v1 = __ldg(g.col + e);
+    }
+    // lane i: CSR range [lb, le) of v_i and lu, the first entry above v_i
+    uint64_t lb = 0, le = 0, lu = 0;
+    if (lane == 0) {
+        lb = __ldg(g.row_ptr + v0);
+        le = __ldg(g.row_ptr + v0 + 1);
+        lu = __ldg(g.up + v0);
+        wm.v[0] = v0;
+        wm.v[1] = v1;
+    } else if (lane == 1) {
+        lb = __ldg(g.row_ptr + v1);
+        le = __ldg(g.row_ptr + v1 + 1);
+        lu = __ldg(g.up + v1);
+    }
+    __syncwarp();
+    out.depth = 2;
+    double w = (double)M;
+    uint64_t wu = M;
+    bool ovf = false;
+    uint32_t prev_size = 0;
+    bool prev_mat = false;
+
+    for (int j = 2; j < k; j++) {
+        const uint32_t lm = p.lower[j];
+        const bool has_lo = lm != 0;
+        uint32_t lo = 0;
+        for (int i = 0; i < j; i++)
+            if ((lm >> i) & 1u) lo = wm.v[i] > lo ? wm.v[i] : lo;
+        const uint64_t r = word(j - 1);
+        // first index of position i's list [b, en) above the lower bound; the
+        // split at lu and the known slot of v1 in N(v0) shorten or skip the search
+        auto above = [&](int i, uint64_t b, uint64_t en) -> uint64_t {
+            const uint64_t ui = __shfl_sync(kFull, lu, i);
+            if (!has_lo) return b;
+            const uint32_t vi = wm.v[i];
+            if (lo == vi) return ui;
+            if (i == 0 && lo == wm.v[1] && pos01 != ~0ull) return pos01 + 1;
+            if (lo > vi) return ui + warp_upper_bound(g.col + ui, en - ui, lo);
+            return b + warp_upper_bound(g.col + b, ui - b, lo);
+        };
+        uint64_t size = 0;
+        uint32_t x = 0;
+        if (MODE == MODE_CHECK) {
+            const int pb = (int)p.last_back[j];
+            const uint64_t b = __shfl_sync(kFull, lb, pb);
+            const uint64_t en = __shfl_sync(kFull, le, pb);
+            const uint64_t start = above(pb, b, en);
+            size = en - start;
+            if (lane == 0) wm.fac[j] = size;
+            if (size == 0) {
+                out.depth = j;
+                return out;
+            }
+            x = __ldg(g.col + start + index_map(r, size));
+            bool okl = true;
+            if ((int)lane < j) {
+                okl = (x != wm.v[lane]);
+                const bool edge = (p.back[j] >> lane) & 1u;
+                if (edge) {
+                    if ((int)lane != pb) okl = okl && lane_contains(g.col + lb, le - lb, x);
+                } else if (p.induced) {
+                    okl = okl && !lane_contains(g.col + lb, le - lb, x);
+                }
+            }
+            if (!__all_sync(kFull, okl)) {
+                out.depth = j;
+                return out;
+            }
+        } else {
+            uint32_t *Sc = (j & 1) ? wm.S1 : wm.S0;
+            uint32_t *Sp = (j & 1) ? wm.S0 : wm.S1;
+            uint64_t count = 0;
+            bool mat = true;
+            if (p.reuse[j] && prev_mat) {
+                // S_j = S_{j-1} (on chip) cut by N(v_{j-1}) above the bound
+                const uint64_t b = __shfl_sync(kFull, lb, j - 1);
+                const uint64_t en = __shfl_sync(kFull, le, j - 1);
+                const uint64_t start = above(j - 1, b, en);
+                const uint64_t L = en > start ? en - start : 0;
+                const uint32_t P = prev_size;
+                if (L <= 8ull * P + 32) {
+                    for (uint64_t base = start; base < en; base += 128) {
+                        uint32_t y[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const uint64_t idx = base + 32 * u + lane;
+                            y[u] = idx < en ? __ldg(g.col + idx) : 0u;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const bool ok = (base + 32 * u + lane < en) && lane_contains_shared(Sp, P, y[u]);
+                            const unsigned m = __ballot_sync(kFull, ok);
+                            if (ok) Sc[count + __popc(m & lanemask_lt())] = y[u];
+                            count += __popc(m);
+                        }
+                    }
+                } else {
+                    for (uint32_t base = 0; base < P; base += 32) {
+                        const uint32_t idx = base + lane;
+                        const bool valid = idx < P;
+                        const uint32_t y = valid ? Sp[idx] : 0u;
+                        const bool ok = valid && (!has_lo || y > lo) && lane_contains(g.col + start, L, y);
+                        const unsigned m = __ballot_sync(kFull, ok);
+                        if (ok) Sc[count + __popc(m & lanemask_lt())] = y;
+                        count += __popc(m);
+                    }
+                }
+            } else {
+                // driver: shortest back-neighbour list, streamed; partner: the
+                // next shortest, staged on chip when its part above the bound fits
+                const uint32_t back = p.back[j];
+                const bool isback = (int)lane < j && ((back >> lane) & 1u);
+                const uint64_t key = isback ? (((le - lb) << 5) | lane) : ~0ull;
+                const int driver = (int)(warp_min_u64(key) & 31u);
+                const uint64_t key2 = warp_min_u64((int)lane == driver ? ~0ull : key);
+                const int partner = (key2 == ~0ull) ? -1 : (int)(key2 & 31u);
+                const uint64_t db = __shfl_sync(kFull, lb, driver);
+                const uint64_t de = __shfl_sync(kFull, le, driver);
+                const uint64_t dstart = above(driver, db, de);
+                bool empty = dstart >= de;
+                int staged = -1;
+                uint32_t plen = 0;
+                if (partner >= 0 && !empty) {
+                    const uint64_t pb0 = __shfl_sync(kFull, lb, partner);
+                    const uint64_t pe = __shfl_sync(kFull, le, partner);
+                    const uint64_t ps = above(partner, pb0, pe);
+                    if (ps >= pe) {
+                        empty = true;
+                    } else if (pe - ps <= a.cap) {
+                        for (uint64_t base = ps; base < pe; base += 128) {
+                            uint32_t y[4];
+#pragma unroll
+                            for (int u = 0; u < 4; u++) {
+                                const uint64_t idx = base + 32 * u + lane;
+                                y[u] = idx < pe ? __ldg(g.col + idx) : 0u;
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; u++) {
+                                const uint64_t idx = base + 32 * u + lane;
+                                if (idx < pe) Sp[idx - ps] = y[u];
+                            }
+                        }
+                        staged = partner;
+                        plen = (uint32_t)(pe - ps);
+                        __syncwarp();
+                    }
+                }
+                // every condition of S_j but membership in the driver list
+                auto pred = [&](uint32_t y) -> bool {
+                    bool ok = true;
+                    for (int i = 0; i < j; i++) {
+                        const uint64_t b = __shfl_sync(kFull, lb, i);
+                        const uint64_t en2 = __shfl_sync(kFull, le, i);
+                        ok = ok && (y != wm.v[i]);
+                        const bool edge = (back >> i) & 1u;
+                        if (edge) {
+                            if (i == driver) continue;
+                            if (i == staged) ok = ok && lane_contains_shared(Sp, plen, y);
+                            else ok = ok && lane_contains(g.col + b, en2 - b, y);
+                        } else if (p.induced) {
+                            ok = ok && !lane_contains(g.col + b, en2 - b, y);
+                        }
+                    }
+                    return ok;
+                };
+                if (!empty) {
+                    for (uint64_t base = dstart; base < de; base += 128) {
+                        uint32_t y[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const uint64_t idx = base + 32 * u + lane;
+                            y[u] = idx < de ? __ldg(g.col + idx) : 0u;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            if (base + 32 * u >= de) break;
+                            const bool ok = pred(y[u]) && (base + 32 * u + lane < de);
+                            const unsigned m = __ballot_sync(kFull, ok);
+                            if (ok) {
+                                const uint64_t pos = count + __popc(m & lanemask_lt());
+                                if (pos < a.cap) Sc[pos] = y[u];
+                            }
+                            count += __popc(m);
+                        }
+                    }
+                    mat = count <= a.cap;
+                    if (!mat) {
+                        // second pass: locate the drawn element without storing the set
+                        const uint64_t target = index_map(r, count);
+                        uint64_t seen = 0;
+                        bool found = false;
+                        for (uint64_t base = dstart; base < de && !found; base += 128) {
+                            uint32_t y[4];
+#pragma unroll
+                            for (int u = 0; u < 4; u++) {
+                                const uint64_t idx = base + 32 * u + lane;
+                                y[u] = idx < de ? __ldg(g.col + idx) : 0u;
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; u++) {
+                                if (found || base + 32 * u >= de) break;
+                                const bool ok = pred(y[u]) && (base + 32 * u + lane < de);
+                                const unsigned m = __ballot_sync(kFull, ok);
+                                const uint64_t c = __popc(m);
+                                if (seen + c > target) {
+                                    const uint32_t rank = (uint32_t)(target - seen);
+                                    const bool mine = ok && (uint32_t)__popc(m & lanemask_lt()) == rank;
+                                    const int src = __ffs(__ballot_sync(kFull, mine)) - 1;
+                                    x = __shfl_sync(kFull, y[u], src);
+                                    found = true;
+                                }
+                                seen += c;
+                            }
+                        }
+                    }
+                }
+            }
+            size = count;
+            if (lane == 0) wm.fac[j] = size;
+            if (size == 0) {
+                out.depth = j;
+                return out;
+            }
+            __syncwarp();
+            if (mat) x = Sc[index_map(r, size)];
+            prev_size = (uint32_t)(mat ? size : 0);
+            prev_mat = mat;
+        }
+        if (lane == 0) wm.v[j] = x;
+        if ((int)lane == j && j + 1 < k) {
+            lb = __ldg(g.row_ptr + x);
+            le = __ldg(g.row_ptr + x + 1);
+            lu = __ldg(g.up + x);
+        }
+        __syncwarp();
+        w = __dmul_rn(w, (double)size);
+        if (__umul64hi(wu, size) != 0) ovf = true;
+        wu = wu * size;
+        out.depth = j + 1;
+    }
+    out.hit = true;
+    out.depth = k;
+    out.w = w;
+    out.wu = ovf ? 0 : wu;
+    out.overflow = ovf;
+    return out;
+}
+
+// ------------------------------------------------------------------ launch shape
+struct Shape {
+    uint32_t blocks, warps, cap, chunk;
+};
+
+inline size_t smem_bytes(const Shape &sh) {
+    return (size_t)sh.warps * (kWarpHeaderWords + 2 * sh.cap) * sizeof(uint32_t);
+}
+
+// Samples per chunk is fixed, so per-chunk partials (and every FP64 total
+// built from them in chunk order) are the same for every launch shape.
+constexpr uint32_t kChunk = 64;
+
+inline Shape pick_shape(gpm_graph *h, const gpm_config *cfg, uint64_t count) {
+    (void)h;
+    (void)count;
+    Shape sh;
+    sh.warps = (cfg && cfg->block_warps) ? (cfg->block_warps < 8 ? cfg->block_warps : 8) : 8;
+    sh.cap = (cfg && cfg->cap) ? cfg->cap : 512;
+    sh.blocks = (cfg && cfg->grid_blocks) ? cfg->grid_blocks : 0;
+    sh.chunk = kChunk;
+    return sh;
+}
+
+}  // namespace gpm
