@@ -42,6 +42,8 @@
 
 #define OG_MAXK 12
 #define OG_MAXRES 66
+/* learned proposal: candidate sets above this size are drawn uniformly */
+#define OG_LEARNED_MAX 256
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10, written from its published definition (SC'11).  Each round */
@@ -452,6 +454,15 @@ static float og_bf16(uint16_t b)
     return f;
 }
 
+/* Learned proposal (not in the paper): at step j <= k-2 with 0 < |S_j| <= 256
+ * each candidate x gets the integer score a_x from the MLP below on the
+ * features (log2(1 + d(x)), j, log2(1 + |S_{j+1}(x)|)), where S_{j+1}(x) is the
+ * next candidate set if x were chosen; x is drawn with probability a_x / A,
+ * A = sum of the scores (the integer CDF in candidate order), and the weight
+ * takes the factor A / a_x.  Every a_x >= 1, so each match keeps a positive
+ * probability whose inverse is its weight (Lemma 1's argument).  Larger sets,
+ * and the last step, are drawn uniformly. */
+
 /* MLP 3 -> 64 -> 64 -> 1 with ReLU, BF16 weights, FP32 FMA chains in input
  * order; the output z is mapped to a score without exp: s = clamp(z/8 + 1/2),
  * a = 1 + floor(4096 s) in [1, 4097]. */
@@ -518,7 +529,8 @@ int og_sample(const og_graph *g, const og_plan *p, const uint64_t *r, int mode,
             if (!og_member(g, p, v, j, x)) { rec->depth = (uint8_t)j; return 0; }
             w = w * (double)size;
             if (__builtin_mul_overflow(wu, size, &wu)) overflow = 1;
-        } else if (mode == OG_LEARNED && j <= p->k - 2) {
+        } else if (mode == OG_LEARNED && j <= p->k - 2 &&
+                   og_cand(g, p, v, j, NULL) <= OG_LEARNED_MAX) {
             size = og_cand(g, p, v, j, buf);
             rec->factor[j] = 0;
             if (size == 0) { rec->depth = (uint8_t)j; return 0; }

@@ -165,11 +165,8 @@ def enumerate_tree(g, p, mode, mlp=None):
             return
         rr = r + [0] * (k - 1 - len(r))
         rec = O.sample(g, p, rr, mode, mlp)
-        if mode == O.LEARNED and j <= k - 2:
+        if mode == O.LEARNED and j <= k - 2 and rec.aux[j] > 0:
             A = rec.factor[j]
-            if A == 0:
-                total[0] += prob
-                return
             t = 0
             while t < A:
                 w = _ceil_word(t, A)
@@ -210,7 +207,7 @@ def enumerate_tree(g, p, mode, mlp=None):
 def leaf_weight(rec, k, mode):
     w = Fraction(int(rec.factor[0]))
     for j in range(2, k):
-        if mode == O.LEARNED and j <= k - 2:
+        if mode == O.LEARNED and j <= k - 2 and rec.aux[j] > 0:
             w *= Fraction(int(rec.factor[j]), int(rec.aux[j]))
         else:
             w *= int(rec.factor[j])
@@ -509,3 +506,28 @@ def test_mlp_grad_finite_difference():
         wm[name][idx] -= h
         fd = (O.mlp_loss_grad(wp, feat, label)[0] - O.mlp_loss_grad(wm, feat, label)[0]) / (2 * h)
         assert grads[name][idx] == pytest.approx(fd, rel=2e-2, abs=2e-4), name
+
+
+def test_learned_large_sets_fall_back_to_uniform_and_stay_unbiased():
+    """Candidate sets above 256 entries are drawn uniformly in learned mode;
+    in K_300 the first candidate set of the 4-clique plan exceeds that bound
+    for many first edges, so both kinds of steps occur, and the estimate is
+    unbiased."""
+    rp, col = G.complete(300)
+    g = og(rp, col)
+    p = O.plan(*G.pattern("4-clique"))
+    mlp = random_mlp(5)
+    _, recs = O.ns_run(g, p, seed=3, first=0, count=2000, mode=O.LEARNED, mlp=mlp, trace=True)
+    sizes = recs["factor"][:, 2]
+    learned = recs["aux"][:, 2] > 0
+    uniform = (~learned) & (sizes > 0)
+    assert learned.any() and uniform.any()
+    assert np.all(sizes[uniform] > 256) and np.all(sizes[learned] > 0)
+    # learned steps record A = sum of scores, each score in [1, 4097]
+    assert np.all(recs["aux"][learned, 2] >= 1) and np.all(recs["aux"][learned, 2] <= 4097)
+    N = 8_000
+    acc, _ = O.ns_run(g, p, seed=4, first=0, count=N, mode=O.LEARNED, mlp=mlp)
+    C = math.comb(300, 4)
+    mean = acc.sum / N
+    sd = math.sqrt(max(acc.sumsq / N - mean * mean, 0.0) / N)
+    assert abs(mean - C) < 5 * sd + 1e-9 * C
