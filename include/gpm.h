@@ -89,7 +89,9 @@ typedef struct {
     uint32_t grid_blocks;   /* sampler launch shape overrides (0 = tuned default) */
     uint32_t block_warps;
     uint32_t cap;           /* per-warp on-chip candidate buffer, entries (0 = default) */
-    const gpm_mlp *mlp;     /* GPM_NS_LEARNED: device weights (required) */
+    const gpm_mlp *mlp;     /* learned proposal weights (device); required by GPM_NS_LEARNED and,
+                               when set, selects the learned proposal in gpm_sample_sums,
+                               gpm_sample_sums_static and gpm_trace */
 } gpm_config;
 
 typedef struct {
@@ -206,6 +208,46 @@ gpm_status gpm_trace(gpm_graph *g, const gpm_pattern *pattern, uint64_t seed, ui
 
 /* Exact count of the pattern (the plan's nested loops over every branch). */
 gpm_status gpm_exact_count(gpm_graph *g, const gpm_pattern *pattern, uint64_t *out);
+
+/* ---- learned proposal (not in the paper; see gpm_scheme GPM_NS_LEARNED) ----
+ * At a step j <= k-2 whose candidate set has 1..256 entries, candidate x gets
+ * the score a_x = 1 + floor(4096 clamp(z/8 + 1/2, 0, 1)), z the output of a
+ * 3 -> 64 -> 64 -> 1 ReLU MLP (BF16 weights, FP32 fused multiply-adds in input
+ * order) on the features (log2(1 + deg x), j, log2(1 + |S_{j+1}(x)|)) with
+ * log2(1 + d) taken as the chord between powers of two; x is drawn with
+ * probability a_x / A (A = sum of scores, integer CDF in candidate order) and
+ * the weight takes the factor A / a_x.  Every score is >= 1, so the estimator
+ * stays unbiased (Lemma 1's argument); larger sets and the last step are drawn
+ * uniformly.  Weights: 4481 values in the order w1 [64][3], b1 [64],
+ * w2 [64][64], b2 [64], w3 [64], b3 [1]. */
+
+/* Scores a_x of n feature rows (DEVICE float [n][3]) into DEVICE out [n];
+ * bit-identical to the scores the sampler computes. */
+gpm_status gpm_mlp_scores(gpm_graph *g, const gpm_mlp *mlp, const float *feat, uint64_t n, uint32_t *out);
+
+/* Mean binary cross-entropy on the logits over rows (DEVICE feat [rows][3],
+ * label [rows] in {0, 1}) at FP32 weights w32 (DEVICE, 4481) and its
+ * gradient into DEVICE grad (4481); *loss on the host. */
+gpm_status gpm_mlp_loss_grad(gpm_graph *g, const float *w32, const float *feat, const float *label, uint64_t rows,
+                             float *grad, double *loss);
+
+/* Training rows from plain-NS records (DEVICE, n): for every step
+ * 2 <= j <= k-2 a sample passed, the features of its chosen vertex vert[j]
+ * (the lookahead is factor[j+1]) and label = hit; rows in record then step
+ * order into DEVICE feat [n (k-3)][3] and label; *rows = rows written. */
+gpm_status gpm_proposal_features(gpm_graph *g, const gpm_pattern *pattern, const gpm_sample_record *recs,
+                                 uint64_t n, float *feat, float *label, uint64_t *rows);
+
+/* Trains the proposal on the device: records of `samples` plain-NS samples
+ * (seed), their feature rows, then `epochs` passes of Adam (lr; beta 0.9,
+ * 0.999) over minibatches of `batch` rows of the mean cross-entropy.  w32
+ * (DEVICE, 4481) holds the initial FP32 weights and receives the trained
+ * ones; w16 (DEVICE, 4481) receives their BF16 copies (round to nearest even)
+ * in the gpm_mlp order.  *final_loss: loss of the trained weights over all
+ * rows; *rows_used: row count.  Pattern size k >= 4. */
+gpm_status gpm_train_proposal(gpm_graph *g, const gpm_pattern *pattern, uint64_t seed, uint64_t samples,
+                              uint32_t epochs, uint32_t batch, float lr, float *w32, uint16_t *w16,
+                              double *final_loss, uint64_t *rows_used);
 
 /* Colour sparsification (Sec. 2.2.2): colour every vertex with
  * floor(philox_word0 * c / 2^32) and keep monochromatic edges.  Writes the

@@ -81,6 +81,10 @@ SIGNATURES = [
     ("gpm_sample_sums_static", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), P(Sums)]),
     ("gpm_trace", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), _V]),
     ("gpm_exact_count", _i32, [_V, P(Pattern), P(_u64)]),
+    ("gpm_mlp_scores", _i32, [_V, P(MLP), _V, _u64, _V]),
+    ("gpm_mlp_loss_grad", _i32, [_V, _V, _V, _V, _u64, _V, P(_dbl)]),
+    ("gpm_proposal_features", _i32, [_V, P(Pattern), _V, _u64, _V, _V, P(_u64)]),
+    ("gpm_train_proposal", _i32, [_V, P(Pattern), _u64, _u64, _u32, _u32, C.c_float, _V, _V, P(_dbl), P(_u64)]),
     ("gpm_sparsify", _i32, [_V, _u32, _u64, _u32, _u32, _V, _V, P(_u64)]),
     ("gpm_abort", _i32, [_V]),
     ("gpm_plan", _i32, [P(Pattern), P(_i32), P(_i32), P(_i32), P(_i32), P(_i32)]),

@@ -42,8 +42,9 @@ def config(**kw):
             val = {"intersect": VERIFY_INTERSECT, "check": VERIFY_CHECK}[val]
         setattr(cfg, key, val)
     if mlp is not None:
-        cfg.mlp = C.pointer(mlp.c_struct())
-        cfg._keep = mlp
+        st = mlp.c_struct()
+        cfg.mlp = C.pointer(st)
+        cfg._keep = (mlp, st)
     return cfg
 
 
@@ -172,3 +173,83 @@ def plan(pat):
 
 def normal_quantile(p):
     return _lib.load().gpm_normal_quantile(p)
+
+
+# ------------------------------------------------------------------ learned proposal
+MLP_SIZES = (("w1", 192), ("b1", 64), ("w2", 4096), ("b2", 64), ("w3", 64), ("b3", 1))
+MLP_FLOATS = 4481
+
+
+class Proposal:
+    """Weights of the learned proposal on the GPU: FP32 master copy ``w32`` and
+    the BF16 bit patterns ``w16`` the sampler reads (gpm_mlp order)."""
+
+    def __init__(self, seed=0, device="cuda"):
+        g = torch.Generator()
+        g.manual_seed(int(seed))
+        parts = []
+        for name, n in MLP_SIZES:
+            fan_in = {"w1": 3, "w2": 64, "w3": 64}.get(name)
+            if fan_in:
+                parts.append(torch.randn(n, generator=g) * (2.0 / fan_in) ** 0.5)
+            else:
+                parts.append(torch.zeros(n))
+        self.w32 = torch.cat(parts).float().to(device).contiguous()
+        self.w16 = self.w32.to(torch.bfloat16).view(torch.int16).contiguous()
+
+    def c_struct(self):
+        base = self.w16.data_ptr()
+        ptrs, off = {}, 0
+        for name, n in MLP_SIZES:
+            ptrs[name] = C.c_void_p(base + 2 * off)
+            off += n
+        return _lib.MLP(**{k: v.value for k, v in ptrs.items()})
+
+    def arrays16(self):
+        """Host uint16 arrays (w1 [64,3], b1, w2 [64,64], b2, w3, b3)."""
+        h = self.w16.cpu().numpy().view(np.uint16)
+        out, off = [], 0
+        for name, n in MLP_SIZES:
+            a = h[off:off + n].copy()
+            out.append(a.reshape(64, 3) if name == "w1" else a.reshape(64, 64) if name == "w2" else a)
+            off += n
+        return out
+
+    def train(self, graph, pat, seed=1, samples=1 << 20, epochs=4, batch=8192, lr=3e-3):
+        loss, rows = C.c_double(), C.c_uint64()
+        pp = pattern(pat)
+        check(_lib.load().gpm_train_proposal(graph.h, C.byref(pp), seed, samples, epochs, batch, lr,
+                                             C.c_void_p(self.w32.data_ptr()), C.c_void_p(self.w16.data_ptr()),
+                                             C.byref(loss), C.byref(rows)), "gpm_train_proposal")
+        return loss.value, rows.value
+
+    def scores(self, graph, feat):
+        """Sampler scores a_x of feature rows (CUDA float tensor [n, 3])."""
+        feat = feat.contiguous().float()
+        out = torch.empty(feat.shape[0], dtype=torch.int32, device=feat.device)
+        m = self.c_struct()
+        check(_lib.load().gpm_mlp_scores(graph.h, C.byref(m), C.c_void_p(feat.data_ptr()), feat.shape[0],
+                                         C.c_void_p(out.data_ptr())), "gpm_mlp_scores")
+        return out
+
+    def loss_grad(self, graph, feat, label, w32=None):
+        w = (self.w32 if w32 is None else w32).contiguous()
+        grad = torch.empty(MLP_FLOATS, dtype=torch.float32, device=w.device)
+        loss = C.c_double()
+        check(_lib.load().gpm_mlp_loss_grad(graph.h, C.c_void_p(w.data_ptr()), C.c_void_p(feat.data_ptr()),
+                                            C.c_void_p(label.data_ptr()), feat.shape[0],
+                                            C.c_void_p(grad.data_ptr()), C.byref(loss)), "gpm_mlp_loss_grad")
+        return loss.value, grad
+
+
+def proposal_features(graph, pat, recs_dev, n):
+    """Training rows from device records (torch uint8 buffer of n records)."""
+    pp = pattern(pat)
+    k = pp.k
+    feat = torch.empty((max(n * max(k - 3, 0), 1), 3), dtype=torch.float32, device="cuda")
+    label = torch.empty(max(n * max(k - 3, 0), 1), dtype=torch.float32, device="cuda")
+    rows = C.c_uint64()
+    check(_lib.load().gpm_proposal_features(graph.h, C.byref(pp), C.c_void_p(recs_dev.data_ptr()), n,
+                                            C.c_void_p(feat.data_ptr()), C.c_void_p(label.data_ptr()),
+                                            C.byref(rows)), "gpm_proposal_features")
+    return feat[:rows.value], label[:rows.value]

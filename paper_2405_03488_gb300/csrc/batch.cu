@@ -45,21 +45,16 @@ struct BatchArgs {
     uint64_t seed, window;
     double z;
     uint32_t njobs, cap, chunk, chunks_per_job;
+    gpm_mlp mlp;
 };
 
 template <int MODE>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : 4)
     ns_batch_kernel(const DGraph g, const Plan *__restrict__ plans, const BatchJob *jobs, BatchCtl *ctl,
                     const BatchArgs ba, Partial *partials) {
     extern __shared__ uint64_t smem64[];
-    uint32_t *smem = reinterpret_cast<uint32_t *>(smem64);
-    const unsigned warp = threadIdx.x >> 5, lane = lane_id();
-    uint32_t *base = smem + warp * (kWarpHeaderWords + 2 * ba.cap);
-    WarpMem wm;
-    wm.fac = reinterpret_cast<uint64_t *>(base);
-    wm.v = base + 24;
-    wm.S0 = base + kWarpHeaderWords;
-    wm.S1 = wm.S0 + ba.cap;
+    const unsigned lane = lane_id();
+    WarpMem wm = warp_mem<MODE>(smem64, ba.cap, ba.mlp);
     const uint32_t total = ctl->total_chunks;
     RunArgs a;
     a.seed = ba.seed;
@@ -192,7 +187,7 @@ __global__ void batch_relayout(BatchJob *jobs, BatchCtl *ctl, const BatchArgs ba
 template <int MODE>
 static cudaError_t batch_grid(gpm_graph *h, const Shape &sh, uint32_t *blocks) {
     auto kern = ns_batch_kernel<MODE>;
-    const size_t smem = smem_bytes(sh);
+    const size_t smem = smem_bytes(sh, MODE);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -209,14 +204,13 @@ static cudaError_t batch_grid(gpm_graph *h, const Shape &sh, uint32_t *blocks) {
 
 // Runs the batch to completion; results[q] for job q.
 gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const double *eps, double delta,
-                          uint64_t seed, const gpm_config *cfg, gpm_result *results) {
+                          uint64_t seed, const gpm_config *cfg, gpm_result *results, int mode) {
     const auto t0 = std::chrono::steady_clock::now();
     const uint32_t nj = (uint32_t)plans.size();
     const uint64_t W = (cfg && cfg->window) ? cfg->window : (1ull << 20);
     const uint64_t n_min = (cfg && cfg->n_min) ? cfg->n_min : W;
     const uint64_t n_max = (cfg && cfg->n_max) ? cfg->n_max : (1ull << 40);
     const double max_s = cfg ? cfg->max_seconds : 0.0;
-    const int mode = (cfg && cfg->verify == GPM_VERIFY_CHECK) ? MODE_CHECK : MODE_INTERSECT;
     if (!(delta > 0.0 && delta < 1.0)) {
         set_error("delta must be in (0, 1)");
         return GPM_ERR_ARG;
@@ -226,7 +220,8 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
             set_error("every eps must be > 0");
             return GPM_ERR_ARG;
         }
-    const Shape sh = pick_shape(h, cfg, W);
+    Shape sh = pick_shape(h, cfg, W);
+    if (mode == MODE_LEARNED && sh.cap < kLearnedMax) sh.cap = kLearnedMax;
     const uint64_t cpj = (W + sh.chunk - 1) / sh.chunk;
     if (cpj * nj >= (1ull << 31)) {
         set_error("batch too large for one launch");
@@ -240,6 +235,8 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
     ba.cap = sh.cap;
     ba.chunk = sh.chunk;
     ba.chunks_per_job = (uint32_t)cpj;
+    std::memset(&ba.mlp, 0, sizeof(ba.mlp));
+    if (mode == MODE_LEARNED) ba.mlp = *cfg->mlp;
 
     std::vector<BatchJob> jobs(nj);
     for (uint32_t q = 0; q < nj; q++) {
@@ -304,15 +301,20 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
     uint32_t blocks = 0;
     if (e == cudaSuccess)
-        e = (mode == MODE_CHECK) ? batch_grid<MODE_CHECK>(h, sh, &blocks) : batch_grid<MODE_INTERSECT>(h, sh, &blocks);
+        e = (mode == MODE_CHECK)     ? batch_grid<MODE_CHECK>(h, sh, &blocks)
+            : (mode == MODE_LEARNED) ? batch_grid<MODE_LEARNED>(h, sh, &blocks)
+                                     : batch_grid<MODE_INTERSECT>(h, sh, &blocks);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        const size_t smem = smem_bytes(sh);
+        const size_t smem = smem_bytes(sh, mode);
         for (int r = 0; r < R; r++) {
             // event nodes around each sampler launch time the sampler alone
             cudaEventRecordWithFlags(ev_k[2 * r], cs, cudaEventRecordExternal);
             if (mode == MODE_CHECK)
                 ns_batch_kernel<MODE_CHECK><<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
+            else if (mode == MODE_LEARNED)
+                ns_batch_kernel<MODE_LEARNED>
+                    <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
             else
                 ns_batch_kernel<MODE_INTERSECT>
                     <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
@@ -418,7 +420,8 @@ extern "C" gpm_status gpm_estimate_batch(gpm_graph *h, uint32_t count, const gpm
         }
     }
     h->abort_flag = 0;
-    return batch_estimate(h, plans, eps, delta, seed, cfg, out);
+    const int mode = (cfg && cfg->verify == GPM_VERIFY_CHECK) ? MODE_CHECK : MODE_INTERSECT;
+    return batch_estimate(h, plans, eps, delta, seed, cfg, out, mode);
 }
 
 extern "C" gpm_status gpm_autotune(gpm_graph *h, uint32_t count, const gpm_pattern *patterns, uint64_t seed,
@@ -450,7 +453,8 @@ extern "C" gpm_status gpm_autotune(gpm_graph *h, uint32_t count, const gpm_patte
             t.window = io->window ? io->window : (1ull << 18);
             t.n_min = t.window;
             t.n_max = t.window;
-            gpm_status st = batch_estimate(h, plans, eps.data(), 0.01, seed, &t, res.data());
+            const int mode = (t.verify == GPM_VERIFY_CHECK) ? MODE_CHECK : MODE_INTERSECT;
+            gpm_status st = batch_estimate(h, plans, eps.data(), 0.01, seed, &t, res.data(), mode);
             if (st != GPM_OK && st != GPM_ERR_NOT_CONVERGED) return st;
             if (res[0].t_sample_s < best) {
                 best = res[0].t_sample_s;

@@ -64,7 +64,7 @@ gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colo
                           uint32_t *user_col);
 double normal_quantile(double p);
 gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const double *eps, double delta,
-                          uint64_t seed, const gpm_config *cfg, gpm_result *results);
+                          uint64_t seed, const gpm_config *cfg, gpm_result *results, int mode);
 }  // namespace gpm
 
 // The opaque handle.

@@ -47,16 +47,10 @@
 namespace gpm {
 
 template <int MODE, bool TRACE>
-__global__ void __launch_bounds__(256, 4) ns_kernel(const DGraph g, const Plan p, const RunArgs a) {
+__global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : 4) ns_kernel(const DGraph g, const Plan p, const RunArgs a) {
     extern __shared__ uint64_t smem64[];
-    uint32_t *smem = reinterpret_cast<uint32_t *>(smem64);
-    const unsigned warp = threadIdx.x >> 5, lane = lane_id();
-    uint32_t *base = smem + warp * (kWarpHeaderWords + 2 * a.cap);
-    WarpMem wm;
-    wm.fac = reinterpret_cast<uint64_t *>(base);
-    wm.v = base + 24;
-    wm.S0 = base + kWarpHeaderWords;
-    wm.S1 = wm.S0 + a.cap;
+    const unsigned lane = lane_id();
+    WarpMem wm = warp_mem<MODE>(smem64, a.cap, a.mlp);
     const uint64_t end = a.first + a.count;
     for (;;) {
         unsigned c = 0;
@@ -68,7 +62,10 @@ __global__ void __launch_bounds__(256, 4) ns_kernel(const DGraph g, const Plan p
         double sum = 0.0, sumsq = 0.0;
         uint64_t hits = 0;
         for (uint64_t s = s0; s < s1; s++) {
-            if (TRACE && lane < kMaxK) wm.fac[lane] = 0;
+            if (TRACE && lane < kMaxK) {
+                wm.fac[lane] = 0;
+                wm.aux[lane] = 0;
+            }
             __syncwarp();
             const SampleOut r = sample_one<MODE>(g, p, a, s, wm);
             if (r.hit) {
@@ -82,7 +79,7 @@ __global__ void __launch_bounds__(256, 4) ns_kernel(const DGraph g, const Plan p
                 if (lane < kMaxK) {
                     rec->factor[lane] = wm.fac[lane];
                     rec->vert[lane] = ((int)lane < r.depth && (int)lane < p.k) ? wm.v[lane] : 0xFFFFFFFFu;
-                    rec->aux[lane] = 0;
+                    rec->aux[lane] = wm.aux[lane];
                 }
                 if (lane == 0) {
                     rec->w_u64 = r.hit ? r.wu : 0;
@@ -156,7 +153,7 @@ __global__ void __launch_bounds__(1024) reduce_partials(const Partial *__restric
 template <int MODE, bool TRACE>
 static cudaError_t launch_ns(gpm_graph *h, const Plan &p, const Shape &sh, const RunArgs &a) {
     auto kern = ns_kernel<MODE, TRACE>;
-    const size_t smem = smem_bytes(sh);
+    const size_t smem = smem_bytes(sh, MODE);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -192,6 +189,7 @@ static gpm_status run_block(gpm_graph *h, const Plan &p, int mode, uint64_t seed
                             uint64_t count, const gpm_config *cfg, int accumulate, gpm_sample_record *trace,
                             float *kernel_ms) {
     Shape sh = pick_shape(h, cfg, count);
+    if (mode == MODE_LEARNED && sh.cap < kLearnedMax) sh.cap = kLearnedMax;
     const uint64_t nchunks = (count + sh.chunk - 1) / sh.chunk;
     if (nchunks >= (1ull << 31)) {
         set_error("too many samples in one launch");
@@ -210,6 +208,8 @@ static gpm_status run_block(gpm_graph *h, const Plan &p, int mode, uint64_t seed
     a.cap = sh.cap;
     a.chunk = sh.chunk;
     a.nchunks = (uint32_t)nchunks;
+    std::memset(&a.mlp, 0, sizeof(a.mlp));
+    if (mode == MODE_LEARNED) a.mlp = *cfg->mlp;
     if (cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), h->stream) != cudaSuccess) {
         set_error("cudaMemsetAsync failed");
         return GPM_ERR_CUDA;
@@ -218,6 +218,8 @@ static gpm_status run_block(gpm_graph *h, const Plan &p, int mode, uint64_t seed
     cudaError_t e;
     if (mode == MODE_CHECK)
         e = trace ? launch_ns<MODE_CHECK, true>(h, p, sh, a) : launch_ns<MODE_CHECK, false>(h, p, sh, a);
+    else if (mode == MODE_LEARNED)
+        e = trace ? launch_ns<MODE_LEARNED, true>(h, p, sh, a) : launch_ns<MODE_LEARNED, false>(h, p, sh, a);
     else
         e = trace ? launch_ns<MODE_INTERSECT, true>(h, p, sh, a) : launch_ns<MODE_INTERSECT, false>(h, p, sh, a);
     if (kernel_ms) cudaEventRecord(h->ev1, h->stream);
@@ -250,7 +252,11 @@ static gpm_status plan_or_error(const gpm_pattern *pat, Plan *p) {
     return GPM_OK;
 }
 
-static int mode_of(const gpm_config *cfg) { return (cfg && cfg->verify == GPM_VERIFY_CHECK) ? MODE_CHECK : MODE_INTERSECT; }
+// gpm_sample_sums / gpm_trace: weights in cfg->mlp select the learned proposal
+static int mode_of(const gpm_config *cfg) {
+    if (cfg && cfg->mlp) return MODE_LEARNED;
+    return (cfg && cfg->verify == GPM_VERIFY_CHECK) ? MODE_CHECK : MODE_INTERSECT;
+}
 
 // Phi^-1 by Newton iteration on the complementary error function, solved in
 // the lower tail (where erfc keeps full relative accuracy) and mirrored:
@@ -291,12 +297,40 @@ gpm_status ns_estimate(gpm_graph *h, const Plan &p, double eps, double delta, ui
     }
     h->abort_flag = 0;
     std::vector<Plan> plans(1, p);
-    return batch_estimate(h, plans, &eps, delta, seed, cfg, out);
+    const int mode = (cfg && cfg->verify == GPM_VERIFY_CHECK) ? MODE_CHECK : MODE_INTERSECT;
+    return batch_estimate(h, plans, &eps, delta, seed, cfg, out, mode);
+}
+
+// NS with the learned proposal: the same rounds, candidates drawn by score.
+gpm_status learned_estimate(gpm_graph *h, const Plan &p, double eps, double delta, uint64_t seed,
+                            const gpm_config *cfg, gpm_result *out) {
+    if (!cfg || !cfg->mlp || !cfg->mlp->w1 || !cfg->mlp->b1 || !cfg->mlp->w2 || !cfg->mlp->b2 || !cfg->mlp->w3 ||
+        !cfg->mlp->b3) {
+        set_error("GPM_NS_LEARNED needs cfg->mlp with all six device weight arrays");
+        return GPM_ERR_ARG;
+    }
+    if (!(eps > 0.0) || !(delta > 0.0 && delta < 1.0)) {
+        set_error("eps must be > 0 and delta in (0, 1)");
+        return GPM_ERR_ARG;
+    }
+    h->abort_flag = 0;
+    std::vector<Plan> plans(1, p);
+    gpm_status st = batch_estimate(h, plans, &eps, delta, seed, cfg, out, MODE_LEARNED);
+    out->scheme_used = GPM_NS_LEARNED;
+    return st;
 }
 
 }  // namespace gpm
 
 using namespace gpm;
+
+namespace gpm {
+// Records of samples [first, first + count) into a device buffer.
+gpm_status trace_device(gpm_graph *h, const Plan &p, uint64_t seed, uint64_t first, uint64_t count,
+                        const gpm_config *cfg, gpm_sample_record *d_out) {
+    return run_block(h, p, mode_of(cfg), seed, cfg ? cfg->slot : 0, first, count, cfg, 0, d_out, nullptr);
+}
+}  // namespace gpm
 
 extern "C" gpm_status gpm_sample_sums(gpm_graph *h, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
                                       uint64_t count, const gpm_config *cfg, gpm_sums *out) {
@@ -497,6 +531,8 @@ extern "C" gpm_status gpm_estimate(gpm_graph *h, const gpm_pattern *pattern, gpm
             return ns_estimate(h, p, eps, delta, seed, cfg, out);
         case GPM_GS:
             return gs_estimate(h, p, seed, cfg, out);
+        case GPM_NS_LEARNED:
+            return learned_estimate(h, p, eps, delta, seed, cfg, out);
         case GPM_HYBRID:
             if (!(eps > 0.0) || !(delta > 0.0 && delta < 1.0)) {
                 set_error("eps must be > 0 and delta in (0, 1)");
@@ -593,6 +629,8 @@ extern "C" gpm_status gpm_sample_sums_static(gpm_graph *h, const gpm_pattern *pa
     unsigned int *ctr = reinterpret_cast<unsigned int *>(base + kStaticPartialBytes + 256);
 
     Shape sh = pick_shape(h, cfg, count);
+    const int mode = mode_of(cfg);
+    if (mode == MODE_LEARNED && sh.cap < kLearnedMax) sh.cap = kLearnedMax;
     const uint64_t min_chunk = (count + kStaticMaxChunks - 1) / kStaticMaxChunks;
     if (sh.chunk < min_chunk) sh.chunk = (uint32_t)min_chunk;
     const uint64_t nchunks = (count + sh.chunk - 1) / sh.chunk;
@@ -607,10 +645,13 @@ extern "C" gpm_status gpm_sample_sums_static(gpm_graph *h, const gpm_pattern *pa
     a.cap = sh.cap;
     a.chunk = sh.chunk;
     a.nchunks = (uint32_t)nchunks;
+    std::memset(&a.mlp, 0, sizeof(a.mlp));
+    if (mode == MODE_LEARNED) a.mlp = *cfg->mlp;
     cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess)
-        e = (mode_of(cfg) == MODE_CHECK) ? launch_ns<MODE_CHECK, false>(h, p, sh, a)
-                                         : launch_ns<MODE_INTERSECT, false>(h, p, sh, a);
+        e = (mode == MODE_CHECK)     ? launch_ns<MODE_CHECK, false>(h, p, sh, a)
+            : (mode == MODE_LEARNED) ? launch_ns<MODE_LEARNED, false>(h, p, sh, a)
+                                     : launch_ns<MODE_INTERSECT, false>(h, p, sh, a);
     if (e == cudaSuccess) {
         reduce_partials<<<1, 1024, 0, h->stream>>>(parts, (uint32_t)nchunks, tot, 0);
         e = cudaGetLastError();

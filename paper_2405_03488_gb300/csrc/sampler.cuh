@@ -10,7 +10,12 @@
 
 namespace gpm {
 
-enum { MODE_INTERSECT = 0, MODE_CHECK = 1 };
+enum { MODE_INTERSECT = 0, MODE_CHECK = 1, MODE_LEARNED = 2 };
+
+constexpr uint32_t kLearnedMax = 256;   // larger candidate sets are drawn uniformly
+constexpr int kMlpFloats = 4481;        // 3->64->64->1 weights and biases
+constexpr int kMlpSmemFloats = 4482;    // padded to 8 bytes
+constexpr int kLearnedWarpWords = 128 + kLearnedMax;   // hidden activations + scores
 
 struct RunArgs {
     uint64_t seed;
@@ -23,15 +28,56 @@ struct RunArgs {
     uint32_t cap;                 // entries per on-chip candidate buffer
     uint32_t chunk;               // samples per chunk
     uint32_t nchunks;
+    gpm_mlp mlp;                  // learned proposal weights (device, BF16)
 };
 
-constexpr int kWarpHeaderWords = 40;   // 12 u64 factors + 16 u32 vertices
+constexpr int kWarpHeaderWords = 52;   // 12 u64 factors + 16 u32 vertices + 12 u32 scores
 
 struct WarpMem {
     uint64_t *fac;
     uint32_t *v;
+    uint32_t *aux;
     uint32_t *S0, *S1;
+    float *hbuf;           // learned: 64 + 64 hidden activations
+    uint32_t *score;       // learned: a_x of each candidate
+    const float *W;        // learned: block copy of the weights (W2 transposed)
 };
+
+// Block-level setup: the learned weights (BF16 -> FP32, W2 stored transposed
+// so lanes reading one input column hit distinct banks) and each warp's slices.
+template <int MODE>
+__device__ __forceinline__ WarpMem warp_mem(uint64_t *smem64, uint32_t cap, const gpm_mlp &mlp) {
+    uint32_t *smem = reinterpret_cast<uint32_t *>(smem64);
+    float *W = reinterpret_cast<float *>(smem);
+    if (MODE == MODE_LEARNED) {
+        auto bf = [](const uint16_t *p, int i) { return __uint_as_float((uint32_t)p[i] << 16); };
+        for (int i = threadIdx.x; i < kMlpFloats; i += blockDim.x) {
+            if (i < 192) W[i] = bf(mlp.w1, i);
+            else if (i < 256) W[i] = bf(mlp.b1, i - 192);
+            else if (i < 4352) {
+                const int t = i - 256, o = t >> 6, in = t & 63;
+                W[256 + in * 64 + o] = bf(mlp.w2, t);
+            } else if (i < 4416) W[i] = bf(mlp.b2, i - 4352);
+            else if (i < 4480) W[i] = bf(mlp.w3, i - 4416);
+            else W[i] = bf(mlp.b3, 0);
+        }
+        __syncthreads();
+        smem += kMlpSmemFloats;
+    }
+    const unsigned warp = threadIdx.x >> 5;
+    const uint32_t per = kWarpHeaderWords + 2 * cap + (MODE == MODE_LEARNED ? kLearnedWarpWords : 0);
+    uint32_t *base = smem + warp * per;
+    WarpMem wm;
+    wm.fac = reinterpret_cast<uint64_t *>(base);
+    wm.v = base + 24;
+    wm.aux = base + 40;
+    wm.S0 = base + kWarpHeaderWords;
+    wm.S1 = wm.S0 + cap;
+    wm.hbuf = reinterpret_cast<float *>(wm.S1 + cap);
+    wm.score = wm.S1 + cap + 128;
+    wm.W = W;
+    return wm;
+}
 
 __device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
 #pragma unroll
@@ -44,20 +90,166 @@ __device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
 
-// Conditions of S_j other than membership in the driver list.
-__device__ __forceinline__ bool cand_ok(const DGraph &g, const Plan &p, const uint32_t *v, int j, int driver,
-                                        uint64_t lb, uint64_t le, uint32_t x) {
-    bool ok = true;
-    const uint32_t back = p.back[j];
-    for (int i = 0; i < j; i++) {
-        const uint64_t b = __shfl_sync(kFull, lb, i);
-        const uint64_t e = __shfl_sync(kFull, le, i);
-        ok = ok && (x != v[i]);
-        const bool edge = (back >> i) & 1u;
-        if (edge && i != driver) ok = ok && lane_contains(g.col + b, e - b, x);
-        else if (!edge && p.induced) ok = ok && !lane_contains(g.col + b, e - b, x);
+// log2(1 + d) as the chord between powers of two: e + (y - 2^e) / 2^e with
+// y = d + 1 and e = floor(log2 y), every operation correctly rounded in FP32.
+__device__ __forceinline__ float flog2p1(uint64_t d) {
+    const uint64_t y = d + 1;
+    const int e = 63 - __clzll((long long)y);
+    const uint64_t p2 = 1ull << e;
+    const float frac = __fdiv_rn(__ull2float_rn(y - p2), __ull2float_rn(p2));
+    return __fadd_rn(__int2float_rn(e), frac);
+}
+
+// Score of one candidate: the 3 -> 64 -> 64 -> 1 ReLU MLP with FP32 FMA chains
+// in input order (lane l owns hidden units l and l + 32), the output mapped
+// without exp to s = clamp(z / 8 + 1/2, 0, 1) and a = 1 + floor(4096 s).
+__device__ __forceinline__ uint32_t mlp_score(const WarpMem &wm, float f0, float f1, float f2) {
+    const unsigned lane = lane_id();
+    const float *w1 = wm.W, *b1 = wm.W + 192, *w2t = wm.W + 256, *b2 = wm.W + 4352, *w3 = wm.W + 4416,
+                *b3 = wm.W + 4480;
+    float *h1 = wm.hbuf, *h2 = wm.hbuf + 64;
+#pragma unroll
+    for (int hh = 0; hh < 2; hh++) {
+        const int o = lane + 32 * hh;
+        float acc = b1[o];
+        acc = __fmaf_rn(w1[o * 3 + 0], f0, acc);
+        acc = __fmaf_rn(w1[o * 3 + 1], f1, acc);
+        acc = __fmaf_rn(w1[o * 3 + 2], f2, acc);
+        h1[o] = acc > 0.f ? acc : 0.f;
     }
-    return ok;
+    __syncwarp();
+    float r2[2];
+#pragma unroll
+    for (int hh = 0; hh < 2; hh++) {
+        const int o = lane + 32 * hh;
+        float acc = b2[o];
+        for (int i = 0; i < 64; i++) acc = __fmaf_rn(w2t[i * 64 + o], h1[i], acc);
+        r2[hh] = acc > 0.f ? acc : 0.f;
+    }
+    h2[lane] = r2[0];
+    h2[lane + 32] = r2[1];
+    __syncwarp();
+    float z = b3[0];
+    for (int i = 0; i < 64; i++) z = __fmaf_rn(w3[i], h2[i], z);
+    __syncwarp();
+    float sc = __fmaf_rn(z, 0.125f, 0.5f);
+    if (!(sc > 0.f)) sc = 0.f;
+    if (sc > 1.f) sc = 1.f;
+    return 1u + (uint32_t)floorf(__fmul_rn(sc, 4096.0f));
+}
+
+// |S_{j+1}| if candidate Sj[ix] were chosen as v_j.  When S_{j+1} extends S_j
+// by one adjacency it is counted from S_j on chip (elements above the new
+// bound that lie in N(x)); otherwise every condition is tested on the lists.
+static __device__ __noinline__ uint64_t lookahead_count(const DGraph &g, const Plan &p, const WarpMem &wm,
+                                                 const uint32_t *Sj, uint32_t sz, uint32_t ix, int j, uint64_t lb,
+                                                 uint64_t le) {
+    const unsigned lane = lane_id();
+    const int jj = j + 1;
+    const uint32_t x = Sj[ix];
+    const uint64_t xb = __ldg(g.row_ptr + x), xe = __ldg(g.row_ptr + x + 1), xu = __ldg(g.up + x);
+    const uint32_t lm = p.lower[jj];
+    const bool has_lo = lm != 0;
+    uint32_t lo = 0;
+    for (int i = 0; i < jj; i++)
+        if ((lm >> i) & 1u) {
+            const uint32_t vi = (i == j) ? x : wm.v[i];
+            lo = vi > lo ? vi : lo;
+        }
+    uint64_t cnt = 0;
+    if (p.reuse[jj]) {
+        uint32_t s0 = 0;
+        if (has_lo)
+            for (uint32_t base = 0; base < sz; base += 32) {
+                const uint32_t idx = base + lane;
+                s0 += __popc(__ballot_sync(kFull, idx < sz && Sj[idx] <= lo));
+            }
+        const uint32_t P = sz - s0;
+        if (P == 0) return 0;
+        uint64_t ls = xb;
+        if (has_lo) {
+            if (lo == x) ls = xu;
+            else if (lo > x) ls = xu + warp_upper_bound(g.col + xu, xe - xu, lo);
+            else ls = xb + warp_upper_bound(g.col + xb, xu - xb, lo);
+        }
+        const uint64_t L = xe > ls ? xe - ls : 0;
+        if (L <= 8ull * P + 32) {
+            for (uint64_t base = ls; base < xe; base += 32) {
+                const uint64_t idx = base + lane;
+                const bool ok = idx < xe && lane_contains_shared(Sj + s0, P, __ldg(g.col + idx));
+                cnt += __popc(__ballot_sync(kFull, ok));
+            }
+        } else {
+            for (uint32_t base = 0; base < P; base += 32) {
+                const uint32_t idx = base + lane;
+                const bool ok = idx < P && lane_contains(g.col + ls, L, Sj[s0 + idx]);
+                cnt += __popc(__ballot_sync(kFull, ok));
+            }
+        }
+        return cnt;
+    }
+    const uint64_t mb = ((int)lane == j) ? xb : lb, me = ((int)lane == j) ? xe : le;
+    const uint32_t back = p.back[jj];
+    const uint64_t key = ((int)lane < jj && ((back >> lane) & 1u)) ? (((me - mb) << 5) | lane) : ~0ull;
+    const int d = (int)(warp_min_u64(key) & 31u);
+    const uint64_t db = __shfl_sync(kFull, mb, d), de = __shfl_sync(kFull, me, d);
+    const uint64_t start = has_lo ? db + warp_upper_bound(g.col + db, de - db, lo) : db;
+    for (uint64_t base = start; base < de; base += 32) {
+        const uint64_t idx = base + lane;
+        const bool valid = idx < de;
+        const uint32_t y = valid ? __ldg(g.col + idx) : 0u;
+        bool ok = true;
+        for (int i = 0; i < jj; i++) {
+            const uint64_t bi = __shfl_sync(kFull, mb, i), ei = __shfl_sync(kFull, me, i);
+            const uint32_t vi = (i == j) ? x : wm.v[i];
+            ok = ok && (y != vi);
+            const bool edge = (back >> i) & 1u;
+            if (edge && i != d) ok = ok && lane_contains(g.col + bi, ei - bi, y);
+            else if (!edge && p.induced) ok = ok && !lane_contains(g.col + bi, ei - bi, y);
+        }
+        cnt += __popc(__ballot_sync(kFull, ok && valid));
+    }
+    return cnt;
+}
+
+// Learned draw over the materialised S_j: scores a_x of every candidate, A =
+// their sum, t = floor(r A / 2^64), the smallest index whose score prefix
+// exceeds t.
+static __device__ __noinline__ uint32_t learned_pick(const DGraph &g, const Plan &p, const WarpMem &wm, const uint32_t *Sj,
+                                              uint32_t sz, int j, uint64_t r, uint64_t lb, uint64_t le,
+                                              uint64_t *A_out, uint32_t *a_out) {
+    const unsigned lane = lane_id();
+    uint64_t A = 0;
+    for (uint32_t i = 0; i < sz; i++) {
+        const uint32_t x = Sj[i];
+        const uint64_t nxt = lookahead_count(g, p, wm, Sj, sz, i, j, lb, le);
+        const uint64_t dx = __ldg(g.row_ptr + x + 1) - __ldg(g.row_ptr + x);
+        const uint32_t a = mlp_score(wm, flog2p1(dx), __int2float_rn(j), flog2p1(nxt));
+        if (lane == 0) wm.score[i] = a;
+        A += a;
+    }
+    __syncwarp();
+    const uint64_t t = index_map(r, A);
+    uint64_t run = 0;
+    uint32_t chosen = 0;
+    for (uint32_t base = 0; base < sz; base += 32) {
+        const uint32_t idx = base + lane;
+        uint64_t inc = idx < sz ? wm.score[idx] : 0;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+            const uint64_t t2 = __shfl_up_sync(kFull, inc, dd);
+            if ((int)lane >= dd) inc += t2;
+        }
+        const unsigned m = __ballot_sync(kFull, idx < sz && run + inc > t);
+        if (m) {
+            chosen = base + __ffs(m) - 1;
+            break;
+        }
+        run += __shfl_sync(kFull, inc, 31);
+    }
+    *A_out = A;
+    *a_out = wm.score[chosen];
+    return Sj[chosen];
 }
 
 // Result of one sample, uniform across the warp.
@@ -154,6 +346,8 @@ __device__ SampleOut sample_one(const DGraph &g, const Plan &p, const RunArgs &a
         };
         uint64_t size = 0;
         uint32_t x = 0;
+        bool learned_step = false;
+        double lfac = 1.0;
         if (MODE == MODE_CHECK) {
             const int pb = (int)p.last_back[j];
             const uint64_t b = __shfl_sync(kFull, lb, pb);
@@ -336,7 +530,19 @@ __device__ SampleOut sample_one(const DGraph &g, const Plan &p, const RunArgs &a
                 return out;
             }
             __syncwarp();
-            if (mat) x = Sc[index_map(r, size)];
+            if (MODE == MODE_LEARNED && j <= k - 2 && mat && size <= kLearnedMax) {
+                uint64_t A = 0;
+                uint32_t ax = 0;
+                x = learned_pick(g, p, wm, Sc, (uint32_t)size, j, r, lb, le, &A, &ax);
+                if (lane == 0) {
+                    wm.fac[j] = A;
+                    wm.aux[j] = ax;
+                }
+                lfac = __ddiv_rn((double)A, (double)ax);
+                learned_step = true;
+            } else if (mat) {
+                x = Sc[index_map(r, size)];
+            }
             prev_size = (uint32_t)(mat ? size : 0);
             prev_mat = mat;
         }
@@ -347,15 +553,21 @@ __device__ SampleOut sample_one(const DGraph &g, const Plan &p, const RunArgs &a
             lu = __ldg(g.up + x);
         }
         __syncwarp();
-        w = __dmul_rn(w, (double)size);
-        if (__umul64hi(wu, size) != 0) ovf = true;
-        wu = wu * size;
+        if (learned_step) {
+            w = __dmul_rn(w, lfac);
+        } else {
+            w = __dmul_rn(w, (double)size);
+            if (MODE != MODE_LEARNED) {
+                if (__umul64hi(wu, size) != 0) ovf = true;
+                wu = wu * size;
+            }
+        }
         out.depth = j + 1;
     }
     out.hit = true;
     out.depth = k;
     out.w = w;
-    out.wu = ovf ? 0 : wu;
+    out.wu = (MODE == MODE_LEARNED || ovf) ? 0 : wu;
     out.overflow = ovf;
     return out;
 }
@@ -365,8 +577,10 @@ struct Shape {
     uint32_t blocks, warps, cap, chunk;
 };
 
-inline size_t smem_bytes(const Shape &sh) {
-    return (size_t)sh.warps * (kWarpHeaderWords + 2 * sh.cap) * sizeof(uint32_t);
+inline size_t smem_bytes(const Shape &sh, int mode) {
+    const size_t per = kWarpHeaderWords + 2 * sh.cap + (mode == MODE_LEARNED ? kLearnedWarpWords : 0);
+    return (size_t)sh.warps * per * sizeof(uint32_t) +
+           (mode == MODE_LEARNED ? kMlpSmemFloats * sizeof(float) : 0);
 }
 
 // Samples per chunk is fixed, so per-chunk partials (and every FP64 total
