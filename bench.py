@@ -2,11 +2,15 @@
 neighbour sampling with eager verify on R-MAT scale 22 (edge factor 16),
 4-clique and 5-clique, through libgpm's C ABI on one GB300.
 
-A step is one full estimate of each pattern to eps = 1%, delta = 1%
-(Algorithm 3 rounds of 2^20 samples until eps_hat <= eps), seed = step index.
-``value`` = samples/s over the timed steps with the graph resident in HBM;
-``e2e`` repeats the steps through the public API from pinned host arrays
-(graph upload and result read-back inside the timed region).
+A step estimates both patterns to eps = 1%, delta = 1% in one batched call
+(Algorithm 3 rounds of 2^20 samples per pattern, one persistent sampler launch
+per round, convergence checked on the device, rounds replayed as a CUDA
+graph), seed = step index.  ``value`` = samples/s over the timed steps with
+the graph resident in HBM; ``e2e`` repeats the steps through the public API
+from pinned host arrays (graph upload and result read-back inside the timed
+region).  After the timed steps the learned proposal is trained per pattern
+on plain-NS traces and both variants are run to the same target on the same
+seeds; that comparison is reported in ``learned_vs_plain``.
 
 --impl reference times the CPU oracle (the reference arm of this project) on
 the host cores over a bounded sample of the same workload.
@@ -41,6 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpm", choices=["gpm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ncu-case", default=None, choices=["4-clique", "5-clique"],
                     help="profiling case: R-MAT 22 resident, --steps sampler launches of one window each")
@@ -117,20 +122,27 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("sampler.cuh", "batch.cu", "device.cuh")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2405_03488_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def ncu_traffic():
     """Per-launch DRAM traffic of the sampler from the committed ncu summary,
-    if it was taken on the current kernel source."""
-    import hashlib
-    summ = os.path.join(ROOT, "profiles", "ns_kernel_rmat22.md")
-    src = os.path.join(ROOT, "paper_2405_03488_gb300", "csrc", "ns.cu")
+    if it was taken on the current kernel sources."""
+    summ = os.path.join(ROOT, "profiles", "ns_batch_kernel_rmat22.md")
     if not os.path.exists(summ):
         return None
     txt = open(summ).read()
     m1 = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
     m2 = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.e+]+)", txt)
-    if not (m1 and m2):
-        return None
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != m1.group(1):
+    if not (m1 and m2) or m1.group(1) != kernel_source_hash():
         return None
     return float(m2.group(1))
 
@@ -197,7 +209,8 @@ def run_reference(args):
         return
     import torch
     from paper_2405_03488_gb300 import graphs as G
-    rp, col = make_graph("cpu")
+    # the same realisation as the GPU arm (generated on the device when present)
+    rp, col = make_graph("cuda" if torch.cuda.is_available() else "cpu")
     rp_np, col_np = G.to_numpy(rp, col)
     del rp, col
     budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
@@ -223,11 +236,40 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ learned vs plain
+def learned_vs_plain(g, api, seed=5):
+    """Per pattern: train the proposal on plain-NS traces (2^20 samples, 3
+    epochs of Adam), then run plain and learned NS to +-1% @ 99% on the same
+    seed, and measure hit rate and per-sample CV^2 on 2^20 further samples."""
+    import torch
+    out = {}
+    for name in PATTERNS:
+        prop = api.Proposal(seed=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss, rows = prop.train(g, name, seed=11, samples=1 << 20, epochs=3, batch=8192, lr=3e-3)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        row = {"train_s": train_s, "train_rows": rows, "train_loss": loss}
+        for variant in ("plain", "learned"):
+            kw = {"mlp": prop} if variant == "learned" else {}
+            sch = api.NS_LEARNED if variant == "learned" else api.NS
+            r = g.estimate(name, scheme=sch, eps=EPS, delta=DELTA, seed=seed, window=WINDOW, n_max=N_MAX, **kw)
+            s = g.sample_sums(name, seed=seed + 1, first=0, count=WINDOW, **kw)
+            mu = s.sum / s.n
+            row[variant] = {"time_to_converge_s": r["t_total_s"], "samples": r["samples"],
+                            "samples_per_s": r["samples"] / max(r["t_sample_s"], 1e-12),
+                            "estimate": r["estimate"], "eps_hat": r["eps_hat"], "hit_rate": s.hits / s.n,
+                            "cv2": (s.sumsq / s.n - mu * mu) / (mu * mu) if mu > 0 else None}
+        out[name] = row
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def ncu_case(args):
     """A small, self-contained case for ncu: the graph stays resident, the
-    generator's temporaries are released, and --steps launches of one window
-    (2^20 samples) of the sampler run after --warmup untimed ones."""
+    generator's temporaries are released, and --warmup + --steps one-round
+    estimates (one batched sampler launch of 2^20 samples each) run."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -237,7 +279,7 @@ def ncu_case(args):
     torch.cuda.empty_cache()
     g = api.Graph(rp, col)
     for s in range(args.warmup + args.steps):
-        g.sample_sums(args.ncu_case, seed=1 + s, first=0, count=WINDOW)
+        g.estimate(args.ncu_case, eps=EPS, delta=DELTA, seed=1 + s, window=WINDOW, n_max=WINDOW)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": args.ncu_case, "launches": args.warmup + args.steps, "window": WINDOW}))
 
@@ -272,12 +314,10 @@ def main():
             torch.distributed.barrier()
 
     def one_step(graph, step):
-        res = {}
-        for name in PATTERNS:
-            # weak scaling: every rank runs its own estimate on its own seed stream
-            res[name] = graph.estimate(name, eps=EPS, delta=DELTA, seed=1 + step + 1000 * rank,
-                                       window=WINDOW, n_max=N_MAX)
-        return res
+        # weak scaling: every rank runs its own estimates on its own seed stream
+        res = graph.estimate_batch(list(PATTERNS), [EPS] * len(PATTERNS), delta=DELTA,
+                                   seed=1 + step + 1000 * rank, window=WINDOW, n_max=N_MAX)
+        return dict(zip(PATTERNS, res))
 
     for w in range(args.warmup):
         one_step(g, w)
@@ -297,9 +337,10 @@ def main():
     elapsed = ev0.elapsed_time(ev1) / 1e3
     barrier()
     samples = sum(r[p]["samples"] for r in per_step for p in PATTERNS)
-    kernel_s = sum(r[p]["t_sample_s"] for r in per_step for p in PATTERNS)
-    rounds = sum(r[p]["rounds"] for r in per_step for p in PATTERNS)
-    launches = sum(r[p]["kernel_launches"] for r in per_step for p in PATTERNS)
+    # one batched call per step: kernel time, rounds and launches are per call
+    kernel_s = sum(r[PATTERNS[0]]["t_sample_s"] for r in per_step)
+    rounds = sum(max(r[p]["rounds"] for p in PATTERNS) for r in per_step)
+    launches = sum(r[PATTERNS[0]]["kernel_launches"] for r in per_step)
     if world > 1:
         t = torch.tensor([elapsed], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -323,12 +364,14 @@ def main():
         r = one_step(gh, s)
         gh.close()
         e2e_samples += sum(r[p]["samples"] for p in PATTERNS)
-        e2e_d2h += sum(r[p]["rounds"] for p in PATTERNS) * 32 + 32
+        # per graph launch the control word (16 B) comes back, at the end the job states
+        e2e_d2h += 16 * ((max(r[p]["rounds"] for p in PATTERNS) + 3) // 4) + 128 * len(PATTERNS) + 32
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
     e2e = {"value": e2e_samples * world / e2e_t, "unit": "samples/s",
            "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz, "d2h_bytes_per_step": e2e_d2h // args.steps}
 
+    learned = learned_vs_plain(g, api) if (rank == 0 and not args.no_learned) else None
     if rank != 0:
         return
     last = per_step[-1]
@@ -338,16 +381,16 @@ def main():
             "config": {"workload": WORKLOAD, "n": n, "m": m, "patterns": list(PATTERNS), "eps": EPS,
                        "delta": DELTA, "window": WINDOW, "n_max": N_MAX,
                        "l2": "inputs larger than L2 (CSR %.2f GB vs 129 MB L2)" % ((8 * (n + 1) + 4 * nnz) / 1e9)},
-            "time_to_converge_s": {p: last[p]["t_total_s"] for p in PATTERNS},
+            "time_to_converge_s": {"batch": last[PATTERNS[0]]["t_total_s"]},
             "samples_to_converge": {p: last[p]["samples"] for p in PATTERNS},
             "estimate": {p: last[p]["estimate"] for p in PATTERNS},
             "eps_hat": {p: last[p]["eps_hat"] for p in PATTERNS},
             "hit_rate": {p: last[p]["hits"] / max(1, last[p]["samples"]) for p in PATTERNS},
-            "e2e": e2e, "gpu_launches": int(launches), "clocks": ck}
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": ck, "learned_vs_plain": learned}
 
     peak, peak_kind = measured_peaks()
     roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
-            "traffic": ncu_traffic(), "kernel": "ns_kernel<INTERSECT>", "peak_kind": peak_kind}
+            "traffic": ncu_traffic(), "kernel": "ns_batch_kernel<INTERSECT>", "peak_kind": peak_kind}
     if world == 1 and not args.no_cpu_baseline:
         ores, wall, cores = oracle_sample(*G.to_numpy(rp, col), args.cpu_seconds)
         cpu_n = sum(v["n"] for v in ores.values())

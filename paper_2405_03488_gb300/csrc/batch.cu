@@ -49,12 +49,15 @@ struct BatchArgs {
 };
 
 template <int MODE>
-__global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : 4)
+__global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOCKS)
     ns_batch_kernel(const DGraph g, const Plan *__restrict__ plans, const BatchJob *jobs, BatchCtl *ctl,
                     const BatchArgs ba, Partial *partials) {
     extern __shared__ uint64_t smem64[];
+    __shared__ StepPlan splan[8];
     const unsigned lane = lane_id();
     WarpMem wm = warp_mem<MODE>(smem64, ba.cap, ba.mlp);
+    StepPlan *sp = &splan[threadIdx.x >> 5];
+    uint32_t cur_job = 0xFFFFFFFFu;
     const uint32_t total = ctl->total_chunks;
     RunArgs a;
     a.seed = ba.seed;
@@ -78,7 +81,11 @@ __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : 4)
         const uint64_t s0 = first + (uint64_t)(c - J.chunk_off) * ba.chunk;
         const uint64_t s1 = (s0 + ba.chunk < end) ? s0 + ba.chunk : end;
         a.slot = J.slot;
-        const Plan &p = plans[job];
+        if (job != cur_job) {
+            load_step_plan(plans[job], sp);
+            cur_job = job;
+        }
+        const StepPlan &p = *sp;
         double sum = 0.0, sumsq = 0.0;
         uint64_t hits = 0;
         for (uint64_t s = s0; s < s1; s++) {

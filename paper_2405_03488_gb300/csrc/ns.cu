@@ -47,7 +47,7 @@
 namespace gpm {
 
 template <int MODE, bool TRACE>
-__global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : 4) ns_kernel(const DGraph g, const Plan p, const RunArgs a) {
+__global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOCKS) ns_kernel(const DGraph g, const Plan p, const RunArgs a) {
     extern __shared__ uint64_t smem64[];
     const unsigned lane = lane_id();
     WarpMem wm = warp_mem<MODE>(smem64, a.cap, a.mlp);

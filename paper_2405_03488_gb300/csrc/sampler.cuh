@@ -12,6 +12,11 @@ namespace gpm {
 
 enum { MODE_INTERSECT = 0, MODE_CHECK = 1, MODE_LEARNED = 2 };
 
+// resident 256-thread blocks per SM the plain sampler kernels are compiled for
+#ifndef GPM_MIN_BLOCKS
+#define GPM_MIN_BLOCKS 4
+#endif
+
 constexpr uint32_t kLearnedMax = 256;   // larger candidate sets are drawn uniformly
 constexpr int kMlpFloats = 4481;        // 3->64->64->1 weights and biases
 constexpr int kMlpSmemFloats = 4482;    // padded to 8 bytes
@@ -30,6 +35,30 @@ struct RunArgs {
     uint32_t nchunks;
     gpm_mlp mlp;                  // learned proposal weights (device, BF16)
 };
+
+// The fields of a Plan the sampler reads, for an on-chip copy per warp.
+struct StepPlan {
+    int32_t k, induced, oriented, pad;
+    uint32_t back[kMaxK], lower[kMaxK], reuse[kMaxK], last_back[kMaxK];
+};
+
+// Copies plan fields into a warp's StepPlan (all lanes call it).
+__device__ __forceinline__ void load_step_plan(const Plan &src, StepPlan *dst) {
+    const unsigned lane = threadIdx.x & 31u;
+    if (lane == 0) {
+        dst->k = src.k;
+        dst->induced = src.induced;
+        dst->oriented = src.oriented;
+        dst->pad = 0;
+    }
+    if (lane < (unsigned)kMaxK) {
+        dst->back[lane] = src.back[lane];
+        dst->lower[lane] = src.lower[lane];
+        dst->reuse[lane] = src.reuse[lane];
+        dst->last_back[lane] = src.last_back[lane];
+    }
+    __syncwarp();
+}
 
 constexpr int kWarpHeaderWords = 52;   // 12 u64 factors + 16 u32 vertices + 12 u32 scores
 
@@ -141,7 +170,8 @@ __device__ __forceinline__ uint32_t mlp_score(const WarpMem &wm, float f0, float
 // |S_{j+1}| if candidate Sj[ix] were chosen as v_j.  When S_{j+1} extends S_j
 // by one adjacency it is counted from S_j on chip (elements above the new
 // bound that lie in N(x)); otherwise every condition is tested on the lists.
-static __device__ __noinline__ uint64_t lookahead_count(const DGraph &g, const Plan &p, const WarpMem &wm,
+template <typename PlanT>
+static __device__ __noinline__ uint64_t lookahead_count(const DGraph &g, const PlanT &p, const WarpMem &wm,
                                                  const uint32_t *Sj, uint32_t sz, uint32_t ix, int j, uint64_t lb,
                                                  uint64_t le) {
     const unsigned lane = lane_id();
@@ -215,7 +245,8 @@ static __device__ __noinline__ uint64_t lookahead_count(const DGraph &g, const P
 // Learned draw over the materialised S_j: scores a_x of every candidate, A =
 // their sum, t = floor(r A / 2^64), the smallest index whose score prefix
 // exceeds t.
-static __device__ __noinline__ uint32_t learned_pick(const DGraph &g, const Plan &p, const WarpMem &wm, const uint32_t *Sj,
+template <typename PlanT>
+static __device__ __noinline__ uint32_t learned_pick(const DGraph &g, const PlanT &p, const WarpMem &wm, const uint32_t *Sj,
                                               uint32_t sz, int j, uint64_t r, uint64_t lb, uint64_t le,
                                               uint64_t *A_out, uint32_t *a_out) {
     const unsigned lane = lane_id();
@@ -260,8 +291,8 @@ struct SampleOut {
     bool hit, overflow;
 };
 
-template <int MODE>
-__device__ SampleOut sample_one(const DGraph &g, const Plan &p, const RunArgs &a, uint64_t s, WarpMem &wm) {
+template <int MODE, typename PlanT>
+__device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &a, uint64_t s, WarpMem &wm) {
     const unsigned lane = lane_id();
     const int k = p.k;
     SampleOut out;
