@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--config", default="rmat22",
+                    choices=["rmat22", "er-triangle", "rmat24-batch", "chunglu-needle", "rmat27"],
+                    help="workload; the default is the headline R-MAT 22 run, the others print one "
+                         "JSON line each for the companion workloads")
     ap.add_argument("--ncu-case", default=None, choices=["4-clique", "5-clique"],
                     help="profiling case: R-MAT 22 resident, --steps sampler launches of one window each")
     return ap.parse_args()
@@ -265,6 +269,124 @@ def learned_vs_plain(g, api, seed=5):
     return out
 
 
+# ------------------------------------------------------------------ companion workloads
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t0
+
+
+def companion(args):
+    """One JSON line per companion workload (1 GPU)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_03488_gb300 import api
+    from paper_2405_03488_gb300 import graphs as G
+    out = {"config": args.config}
+    if args.config == "er-triangle":
+        # G(n = 10^4, p = 0.002), triangle, 10^6 samples with seed 1; exact count for comparison
+        rp, col = G.erdos_renyi(10_000, 0.002, seed=1, device="cuda")
+        g = api.Graph(rp, col)
+        exact = g.exact_count("triangle")
+        for _ in range(args.warmup):
+            g.sample_sums("triangle", seed=1, first=0, count=10 ** 6)
+        s, t = _timed(lambda: g.sample_sums("triangle", seed=1, first=0, count=10 ** 6))
+        mu = s.sum / s.n
+        sd = ((s.sumsq / s.n - mu * mu) / s.n) ** 0.5
+        out.update({"n": g.n, "m": g.m, "samples": s.n, "seconds": t, "samples_per_s": s.n / t,
+                    "estimate": mu, "exact": exact, "rel_err": abs(mu - exact) / exact, "z": (mu - exact) / sd,
+                    "hit_rate": s.hits / s.n, "eps_hat_99": 2.5758293035489004 * sd / mu})
+    elif args.config == "rmat24-batch":
+        # one batched run: 6 connected 4-vertex motifs (vertex-induced) and triangles, eps 0.5/1/2 %
+        rp, col = G.rmat(24, 16, seed=3, device="cuda")
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        g = api.Graph(rp, col)
+        pats, eps, names = [], [], []
+        for e in (0.005, 0.01, 0.02):
+            for nm in G.MOTIFS4 + ["triangle"]:
+                k, edges = G.pattern(nm)
+                pats.append((k, edges, nm != "triangle"))
+                eps.append(e)
+                names.append("%s@%g" % (nm, e))
+        best, tt = _timed(lambda: g.autotune(pats, seed=7, window=1 << 18))
+        for _ in range(args.warmup):
+            g.estimate_batch(pats, eps, seed=100, window=WINDOW, n_max=1 << 32, **best)
+        res, t = _timed(lambda: g.estimate_batch(pats, eps, seed=1, window=WINDOW, n_max=1 << 32, **best))
+        samples = sum(r["samples"] for r in res)
+        out.update({"n": g.n, "m": g.m, "jobs": len(pats), "autotuned": best, "autotune_s": tt,
+                    "time_to_converge_s": t, "samples": samples, "samples_per_s": samples / t,
+                    "kernel_s": res[0]["t_sample_s"], "rounds": max(r["rounds"] for r in res),
+                    "all_converged": all(r["converged"] for r in res),
+                    "per_job": {nm: {"estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"]}
+                                for nm, r in zip(names, res)}})
+    elif args.config == "chunglu-needle":
+        # Chung-Lu, 8M vertices, exponent 2.1, mean degree 20, 200 planted 12-cliques
+        rp, col = G.chung_lu(8_000_000, gamma=2.1, mean_degree=20.0, n_cliques=200, clique_size=12, seed=4,
+                             device="cuda")
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        g = api.Graph(rp, col)
+        out.update({"n": g.n, "m": g.m, "max_degree": g.max_degree})
+        for name in ("7-clique", "8-clique"):
+            row = {}
+            r, te = _timed(lambda: g.estimate(name, scheme=api.EXACT, max_seconds=120.0))
+            exact = r["exact_count"]
+            row["exact"] = {"count": exact, "seconds": te, "complete": bool(r["converged"])}
+            r, t = _timed(lambda: g.estimate(name, eps=EPS, delta=DELTA, seed=1, window=WINDOW, n_max=1 << 32,
+                                             max_seconds=60.0))
+            row["ns"] = {"seconds": t, "estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"],
+                         "converged": r["converged"], "rel_err": abs(r["estimate"] - exact) / max(exact, 1)}
+            r, t = _timed(lambda: g.estimate(name, scheme=api.GS, seed=1, colors=8))
+            row["gs_c8"] = {"seconds": t, "estimate": r["estimate"], "sparsified_count": r["exact_count"],
+                            "rel_err": abs(r["estimate"] - exact) / max(exact, 1), "preproc_s": r["t_preproc_s"]}
+            r, t = _timed(lambda: g.estimate(name, scheme=api.HYBRID, eps=EPS, delta=DELTA, seed=1, window=WINDOW,
+                                             n_max=1 << 32, max_seconds=60.0, colors=8))
+            row["hybrid"] = {"seconds": t, "scheme": {0: "NS", 1: "GS"}.get(r["scheme_used"], r["scheme_used"]),
+                             "estimate": r["estimate"], "pilot_s": r["t_pilot_s"],
+                             "rel_err": abs(r["estimate"] - exact) / max(exact, 1)}
+            prop = api.Proposal(seed=1)
+            (loss, rows), ttrain = _timed(lambda: prop.train(g, name, seed=11, samples=1 << 21, epochs=3,
+                                                             batch=8192, lr=3e-3))
+            r, t = _timed(lambda: g.estimate(name, scheme=api.NS_LEARNED, eps=EPS, delta=DELTA, seed=1,
+                                             window=WINDOW, n_max=1 << 32, max_seconds=60.0, mlp=prop))
+            row["learned"] = {"seconds": t, "train_s": ttrain, "train_rows": rows, "estimate": r["estimate"],
+                              "eps_hat": r["eps_hat"], "samples": r["samples"], "converged": r["converged"],
+                              "rel_err": abs(r["estimate"] - exact) / max(exact, 1)}
+            for variant, kw in (("plain", {}), ("learned", {"mlp": prop})):
+                sm = g.sample_sums(name, seed=9, first=0, count=1 << 22, **kw)
+                mu = sm.sum / sm.n
+                row[variant + "_cv2"] = (sm.sumsq / sm.n - mu * mu) / (mu * mu) if mu > 0 else None
+                row[variant + "_hit_rate"] = sm.hits / sm.n
+            out[name] = row
+    elif args.config == "rmat27":
+        # R-MAT scale 27, edge factor 16: about 2.1 billion undirected edges
+        rp, col = G.rmat(27, 16, seed=5, device="cuda")
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        g, tl = _timed(lambda: api.Graph(rp, col))
+        out.update({"n": g.n, "m": g.m, "load_s": tl, "gpu_mem_gb": torch.cuda.max_memory_allocated() / 1e9})
+        for name in ("5-clique", "4-cycle"):
+            r, t = _timed(lambda: g.estimate(name, eps=EPS, delta=DELTA, seed=1, window=WINDOW, n_max=1 << 34,
+                                             max_seconds=120.0))
+            row = {"ns": {"seconds": t, "estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"],
+                          "samples_per_s": r["samples"] / max(r["t_sample_s"], 1e-12), "converged": r["converged"]}}
+            if name.endswith("clique"):
+                prop = api.Proposal(seed=1)
+                (loss, rows), ttrain = _timed(lambda: prop.train(g, name, seed=11, samples=1 << 20, epochs=2,
+                                                                 batch=8192, lr=3e-3))
+                r, t = _timed(lambda: g.estimate(name, scheme=api.NS_LEARNED, eps=EPS, delta=DELTA, seed=1,
+                                                 window=WINDOW, n_max=1 << 34, max_seconds=120.0, mlp=prop))
+                row["learned"] = {"seconds": t, "train_s": ttrain, "estimate": r["estimate"], "eps_hat": r["eps_hat"],
+                                  "samples": r["samples"], "converged": r["converged"]}
+            out[name] = row
+    print(json.dumps(out))
+
+
 # ------------------------------------------------------------------ GPU arm
 def ncu_case(args):
     """A small, self-contained case for ncu: the graph stays resident, the
@@ -291,6 +413,9 @@ def main():
         return
     if args.ncu_case:
         ncu_case(args)
+        return
+    if args.config != "rmat22":
+        companion(args)
         return
     rank, world, local = dist_env()
     import numpy as np

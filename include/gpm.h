@@ -156,7 +156,9 @@ gpm_status gpm_graph_info(const gpm_graph *g, uint64_t *n, uint64_t *m, uint64_t
  * GPM_HYBRID: a pilot NS round feeds the cost models of Sec. 4.3-4.4 and the
  * faster engine runs (Sec. 5.1, loose mode).  GPM_EXACT: exact count.
  * Returns GPM_ERR_NOT_CONVERGED (result filled) if n_max or max_seconds ends
- * the run first. */
+ * the run first; for GPM_GS and GPM_EXACT, max_seconds bounds the exact
+ * search on the device, and a search stopped by it leaves a lower bound in
+ * exact_count with converged = 0. */
 gpm_status gpm_estimate(gpm_graph *g, const gpm_pattern *pattern, gpm_scheme scheme, double eps,
                         double delta, uint64_t seed, const gpm_config *cfg, gpm_result *out);
 

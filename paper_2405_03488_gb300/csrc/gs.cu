@@ -129,8 +129,18 @@ __device__ __forceinline__ void level_init(const DGraph &g, const Plan &p, const
     __syncwarp();
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// budget_ns > 0: every warp stops once budget_ns have passed since it started
+// (checked at each grab of first edges and every 64 search steps) and raises
+// *timed_out; the total is then a lower bound.
 __global__ void __launch_bounds__(256) exact_kernel(const DGraph g, const Plan p, uint64_t M, unsigned int *counter,
-                                                    uint32_t per_grab, unsigned long long *total) {
+                                                    uint32_t per_grab, unsigned long long *total, uint64_t budget_ns,
+                                                    unsigned int *timed_out) {
     __shared__ Level lev[8][kMaxK];
     __shared__ uint32_t vv[8][kMaxK];
     __shared__ uint32_t buf[8][kMaxK][32];
@@ -139,7 +149,15 @@ __global__ void __launch_bounds__(256) exact_kernel(const DGraph g, const Plan p
     uint32_t *v = vv[warp];
     const int k = p.k;
     unsigned long long acc = 0;
+    const uint64_t t_start = budget_ns ? __shfl_sync(kFull, global_ns(), 0) : 0;
+    bool out_of_time = false;
+    uint32_t steps = 0;
     for (;;) {
+        if (budget_ns) {
+            const uint64_t now = __shfl_sync(kFull, global_ns(), 0);
+            if (now - t_start > budget_ns) out_of_time = true;
+        }
+        if (out_of_time) break;
         unsigned grab = 0;
         if (lane == 0) grab = atomicAdd(counter, 1u);
         grab = __shfl_sync(kFull, grab, 0);
@@ -179,6 +197,13 @@ __global__ void __launch_bounds__(256) exact_kernel(const DGraph g, const Plan p
             int j = 2;
             level_init(g, p, v, j, lb, le, &L[j]);
             while (j >= 2) {
+                if (budget_ns && ((++steps) & 63u) == 0) {
+                    const uint64_t now = __shfl_sync(kFull, global_ns(), 0);
+                    if (now - t_start > budget_ns) {
+                        out_of_time = true;
+                        break;
+                    }
+                }
                 Level &cur = L[j];
                 const bool last = (j == k - 1);
                 if (cur.mask == 0 || last) {
@@ -220,9 +245,11 @@ __global__ void __launch_bounds__(256) exact_kernel(const DGraph g, const Plan p
                 j++;
                 level_init(g, p, v, j, lb, le, &L[j]);
             }
+            if (out_of_time) break;
         }
     }
     if (lane == 0 && acc) atomicAdd(total, acc);
+    if (lane == 0 && out_of_time) atomicExch(timed_out, 1u);
 }
 
 }  // namespace gpm
@@ -231,26 +258,30 @@ using namespace gpm;
 
 namespace gpm {
 
-gpm_status exact_count_plan(gpm_graph *h, const Plan &p, uint64_t *out, float *kernel_ms) {
+gpm_status exact_count_plan(gpm_graph *h, const Plan &p, uint64_t *out, float *kernel_ms, double max_seconds) {
     const uint64_t M = p.oriented ? h->d.m : h->d.nnz;
     unsigned long long *tot = nullptr;
     unsigned int *ctr = nullptr;
     if (cudaMallocAsync((void **)&tot, sizeof(unsigned long long), h->stream) != cudaSuccess ||
-        cudaMallocAsync((void **)&ctr, sizeof(unsigned int), h->stream) != cudaSuccess) {
+        cudaMallocAsync((void **)&ctr, sizeof(unsigned int) * 2, h->stream) != cudaSuccess) {
         set_error("exact count: device allocation failed");
         return GPM_ERR_OOM;
     }
     cudaMemsetAsync(tot, 0, sizeof(unsigned long long), h->stream);
-    cudaMemsetAsync(ctr, 0, sizeof(unsigned int), h->stream);
+    cudaMemsetAsync(ctr, 0, sizeof(unsigned int) * 2, h->stream);
+    const uint64_t budget_ns = max_seconds > 0.0 ? (uint64_t)(max_seconds * 1e9) : 0;
     uint64_t per = M / ((uint64_t)h->sm_count * 8 * 8 * 64) + 1;
     if (per > 64) per = 64;
     if (M / per >= (1ull << 32)) per = M / (1ull << 31) + 1;
     if (kernel_ms) cudaEventRecord(h->ev0, h->stream);
-    if (M > 0) exact_kernel<<<h->sm_count * 8, 256, 0, h->stream>>>(h->d, p, M, ctr, (uint32_t)per, tot);
+    if (M > 0)
+        exact_kernel<<<h->sm_count * 8, 256, 0, h->stream>>>(h->d, p, M, ctr, (uint32_t)per, tot, budget_ns, ctr + 1);
     if (kernel_ms) cudaEventRecord(h->ev1, h->stream);
     cudaError_t e = cudaGetLastError();
     unsigned long long r = 0;
+    unsigned int late = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, tot, sizeof(r), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&late, ctr + 1, sizeof(late), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFreeAsync(tot, h->stream);
     cudaFreeAsync(ctr, h->stream);
@@ -260,6 +291,10 @@ gpm_status exact_count_plan(gpm_graph *h, const Plan &p, uint64_t *out, float *k
     }
     if (kernel_ms) cudaEventElapsedTime(kernel_ms, h->ev0, h->ev1);
     *out = r;
+    if (late) {
+        set_error("exact count: max_seconds reached; the count is a lower bound");
+        return GPM_ERR_NOT_CONVERGED;
+    }
     return GPM_OK;
 }
 
@@ -325,7 +360,15 @@ gpm_status gs_estimate(gpm_graph *h, const Plan &p, uint64_t seed, const gpm_con
     const auto t1 = std::chrono::steady_clock::now();
     uint64_t cp = 0;
     float ms = 0.f;
-    if (st == GPM_OK) st = exact_count_plan(gs, p, &cp, &ms);
+    const double budget = cfg ? cfg->max_seconds : 0.0;
+    gpm_status late = GPM_OK;
+    if (st == GPM_OK) {
+        st = exact_count_plan(gs, p, &cp, &ms, budget);
+        if (st == GPM_ERR_NOT_CONVERGED) {
+            late = st;
+            st = GPM_OK;
+        }
+    }
     if (gs) gpm_free_graph(gs);
     cudaFree(row);
     cudaFree(col);
@@ -335,12 +378,13 @@ gpm_status gs_estimate(gpm_graph *h, const Plan &p, uint64_t seed, const gpm_con
     out->ci_half_width = NAN;
     out->eps_hat = NAN;
     out->scheme_used = GPM_GS;
-    out->converged = 1;
+    out->converged = late == GPM_OK ? 1 : 0;
     out->t_preproc_s = std::chrono::duration<double>(t1 - t0).count();
     out->t_sample_s = ms * 1e-3;
     out->kernel_launches += 7;
     out->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    return GPM_OK;
+    if (late != GPM_OK) set_error("GS: exact count on the sparsified graph hit max_seconds");
+    return late;
 }
 
 }  // namespace gpm
@@ -356,7 +400,7 @@ extern "C" gpm_status gpm_exact_count(gpm_graph *h, const gpm_pattern *pattern, 
         set_error("pattern rejected: " + why);
         return GPM_ERR_ARG;
     }
-    return exact_count_plan(h, p, out, nullptr);
+    return exact_count_plan(h, p, out, nullptr, 0.0);
 }
 
 extern "C" gpm_status gpm_sparsify(gpm_graph *h, uint32_t colors, uint64_t seed, uint32_t colouring, uint32_t slot,

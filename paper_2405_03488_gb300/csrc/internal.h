@@ -57,7 +57,7 @@ void set_error(const std::string &msg);
 
 struct gpm_graph;
 namespace gpm {
-gpm_status exact_count_plan(gpm_graph *h, const Plan &p, uint64_t *out, float *kernel_ms);
+gpm_status exact_count_plan(gpm_graph *h, const Plan &p, uint64_t *out, float *kernel_ms, double max_seconds);
 gpm_status gs_estimate(gpm_graph *h, const Plan &p, uint64_t seed, const gpm_config *cfg, gpm_result *out);
 gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colouring, uint32_t slot,
                           uint64_t **row_out, uint32_t **col_out, uint64_t *kept, uint64_t *user_row,

@@ -543,18 +543,18 @@ extern "C" gpm_status gpm_estimate(gpm_graph *h, const gpm_pattern *pattern, gpm
             const auto t0 = std::chrono::steady_clock::now();
             uint64_t c = 0;
             float ms = 0.f;
-            st = exact_count_plan(h, p, &c, &ms);
-            if (st != GPM_OK) return st;
+            st = exact_count_plan(h, p, &c, &ms, cfg ? cfg->max_seconds : 0.0);
+            if (st != GPM_OK && st != GPM_ERR_NOT_CONVERGED) return st;
             out->estimate = (double)c;
             out->exact_count = c;
             out->ci_half_width = 0.0;
             out->eps_hat = 0.0;
-            out->converged = 1;
+            out->converged = st == GPM_OK ? 1 : 0;
             out->scheme_used = GPM_EXACT;
             out->t_sample_s = ms * 1e-3;
             out->kernel_launches = 1;
             out->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-            return GPM_OK;
+            return st;
         }
         default:
             set_error("gpm_estimate: scheme not available in this build");

@@ -85,3 +85,22 @@ def test_hybrid_returns_a_consistent_engine_result():
     r = g.estimate("7-clique", scheme=api.HYBRID, eps=0.05, delta=0.01, seed=3, window=1 << 16,
                    n_max=1 << 22, colors=2)
     assert r["scheme_used"] in (api.NS, api.GS)
+
+
+def test_exact_count_deadline_returns_a_lower_bound():
+    """max_seconds bounds the exact search on the device: the 7-cliques of K_200
+    (about 2.2e12) cannot be enumerated in 0.2 s, so the call returns
+    NOT_CONVERGED with a partial count instead of running on."""
+    import math
+    import time
+    rp, col = G.complete(200)
+    g = api.Graph(rp.cuda(), col.cuda())
+    t0 = time.perf_counter()
+    r = g.estimate("7-clique", scheme=api.EXACT, max_seconds=0.2)
+    dt = time.perf_counter() - t0
+    assert r["status"] == -5 and r["converged"] == 0
+    assert 0 < r["exact_count"] < math.comb(200, 7)
+    assert dt < 5.0
+    # a small case finishes inside the budget and is exact
+    r = g.estimate("triangle", scheme=api.EXACT, max_seconds=30.0)
+    assert r["converged"] == 1 and r["exact_count"] == math.comb(200, 3)
