@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--config", default="rmat22",
-                    choices=["rmat22", "er-triangle", "rmat24-batch", "chunglu-needle", "rmat27"],
+                    choices=["rmat22", "er-triangle", "rmat24-batch", "chunglu-needle", "rmat27", "selector"],
                     help="workload; the default is the headline R-MAT 22 run, the others print one "
                          "JSON line each for the companion workloads")
     ap.add_argument("--ncu-case", default=None, choices=["4-clique", "5-clique"],
@@ -384,7 +384,73 @@ def companion(args):
                 row["learned"] = {"seconds": t, "train_s": ttrain, "estimate": r["estimate"], "eps_hat": r["eps_hat"],
                                   "samples": r["samples"], "converged": r["converged"]}
             out[name] = row
+    elif args.config == "selector":
+        out.update(selector_study(api, G))
     print(json.dumps(out))
+
+
+def selector_cases(G, device="cuda"):
+    """Synthetic (graph, pattern, colours) cases for the NS/GS selector head."""
+    graphs = {
+        "er-20k": G.erdos_renyi(20_000, 0.001, seed=11, device=device),
+        "er-dense": G.erdos_renyi(2_000, 0.08, seed=12, device=device),
+        "rmat16": G.rmat(16, 16, seed=13, device=device),
+        "rmat18": G.rmat(18, 8, seed=14, device=device),
+        "cl-needle": G.chung_lu(200_000, n_cliques=100, clique_size=10, seed=15, device=device),
+    }
+    pats = ["triangle", "4-clique", "5-clique", "6-clique", "4-cycle", "house"]
+    return [(gname, rc, p, c) for gname, rc in graphs.items() for p in pats for c in (4, 8)]
+
+
+def selector_study(api, G, eps=0.05, delta=0.01, time_cap=10.0):
+    """Label each case by which engine finished first (NS to eps at 1-delta, or
+    one GS colouring), train the selector head on every other case, and compare
+    its choices with the cost-model rule on the held-out cases."""
+    import torch
+    rows, labels, meta = [], [], []
+    handles = {}
+    for gname, (rp, col), pname, c in selector_cases(G):
+        if gname not in handles:
+            handles[gname] = api.Graph(rp, col)
+        g = handles[gname]
+        info = g.hybrid_model(pname, eps=eps, delta=delta, seed=3, window=1 << 16, colors=c)
+        ns, t_ns = _timed(lambda: g.estimate(pname, eps=eps, delta=delta, seed=3, window=1 << 16,
+                                             max_seconds=time_cap))
+        gs, t_gs = _timed(lambda: g.estimate(pname, scheme=api.GS, seed=3, colors=c, max_seconds=time_cap))
+        if not ns["converged"]:
+            t_ns = float("inf")
+        rows.append(info["features"])
+        labels.append(1.0 if t_gs < t_ns else 0.0)
+        meta.append({"graph": gname, "pattern": pname, "colors": c, "t_ns": t_ns, "t_gs": t_gs,
+                     "cost_model_gs": info["cost_model_gs"]})
+    feat = torch.tensor(rows, dtype=torch.float32, device="cuda")
+    lab = torch.tensor(labels, dtype=torch.float32, device="cuda")
+    n = len(rows)
+    train = torch.arange(0, n, 2, device="cuda")
+    test = torch.arange(1, n, 2, device="cuda")
+    g0 = next(iter(handles.values()))
+    sel = api.Proposal(seed=2)
+    loss = sel.train_rows(g0, feat[train], lab[train], epochs=400, batch=64, lr=1e-2)
+    pick = (sel.scores(g0, feat) >= 2049).float()
+
+    def regret(ix, choose):
+        # extra time over the faster engine, summed over the cases
+        tot = 0.0
+        for i in ix:
+            m = meta[i]
+            best = min(m["t_ns"], m["t_gs"])
+            got = m["t_gs"] if choose(i) else m["t_ns"]
+            tot += (got - best) if got != float("inf") else time_cap
+        return tot
+
+    te = test.tolist()
+    acc_sel = float((pick[test] == lab[test]).float().mean())
+    acc_cm = sum(1 for i in te if meta[i]["cost_model_gs"] == labels[i]) / len(te)
+    return {"cases": n, "gs_faster": int(sum(labels)), "train_loss": loss,
+            "heldout_accuracy": {"selector": acc_sel, "cost_model": acc_cm},
+            "heldout_regret_s": {"selector": regret(te, lambda i: pick[i] > 0.5),
+                                 "cost_model": regret(te, lambda i: meta[i]["cost_model_gs"] == 1),
+                                 "always_ns": regret(te, lambda i: False)}}
 
 
 # ------------------------------------------------------------------ GPU arm

@@ -92,7 +92,20 @@ typedef struct {
     const gpm_mlp *mlp;     /* learned proposal weights (device); required by GPM_NS_LEARNED and,
                                when set, selects the learned proposal in gpm_sample_sums,
                                gpm_sample_sums_static and gpm_trace */
+    const gpm_mlp *selector; /* GPM_HYBRID: learned NS/GS selector head (device weights, same
+                               MLP shape); NULL = the cost-model rule decides */
 } gpm_config;
+
+/* What the hybrid choice saw (Sec. 4.3-4.4, 5.1): the pilot's sample count
+ * estimate, the NS cone, the GS prediction and its parts, the time per
+ * sampler step, the triangle estimate, the selector features
+ * (log2(t_gs / t_lo), log2(t_hi / t_lo), log2(n_s), each clamped to +-64) and
+ * both decisions (1 = GS). */
+typedef struct {
+    double n_s, t_lo, t_hi, t_gs, t_pre, t_search, c_step, triangles;
+    float features[3];
+    int32_t cost_model_gs, selector_gs;
+} gpm_hybrid_info;
 
 typedef struct {
     double estimate;        /* mu, the estimated count */
@@ -161,6 +174,19 @@ gpm_status gpm_graph_info(const gpm_graph *g, uint64_t *n, uint64_t *m, uint64_t
  * exact_count with converged = 0. */
 gpm_status gpm_estimate(gpm_graph *g, const gpm_pattern *pattern, gpm_scheme scheme, double eps,
                         double delta, uint64_t seed, const gpm_config *cfg, gpm_result *out);
+
+/* The hybrid choice without running the chosen engine (pilot NS round, cost
+ * models, selector if cfg->selector).  eps and delta as for gpm_estimate. */
+gpm_status gpm_hybrid_model(gpm_graph *g, const gpm_pattern *pattern, double eps, double delta, uint64_t seed,
+                            const gpm_config *cfg, gpm_hybrid_info *out);
+
+/* Trains the MLP on given rows (DEVICE feat [rows][3], label [rows]): `epochs`
+ * passes of Adam (lr; beta 0.9, 0.999) over minibatches of `batch` rows of the
+ * mean cross-entropy on the logits; w32 (DEVICE, 4481) in/out, w16 (DEVICE,
+ * 4481) receives the BF16 copies; *final_loss over all rows.  Used for the
+ * NS/GS selector head. */
+gpm_status gpm_mlp_train(gpm_graph *g, const float *feat, const float *label, uint64_t rows, uint32_t epochs,
+                         uint32_t batch, float lr, float *w32, uint16_t *w16, double *final_loss);
 
 /* Many (pattern, eps) jobs at once: every round is one persistent sampler
  * launch over the chunks of all jobs still running, followed by a per-job

@@ -41,7 +41,18 @@ class Config(C.Structure):
     _fields_ = [("window", C.c_uint64), ("n_min", C.c_uint64), ("n_max", C.c_uint64),
                 ("max_seconds", C.c_double), ("colors", C.c_uint32), ("slot", C.c_uint32),
                 ("verify", C.c_uint32), ("grid_blocks", C.c_uint32), ("block_warps", C.c_uint32),
-                ("cap", C.c_uint32), ("mlp", C.POINTER(MLP))]
+                ("cap", C.c_uint32), ("mlp", C.POINTER(MLP)), ("selector", C.POINTER(MLP))]
+
+
+class HybridInfo(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("n_s", "t_lo", "t_hi", "t_gs", "t_pre", "t_search", "c_step",
+                                           "triangles")] + \
+               [("features", C.c_float * 3), ("cost_model_gs", C.c_int32), ("selector_gs", C.c_int32)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "features"}
+        d["features"] = list(self.features)
+        return d
 
 
 class Result(C.Structure):
@@ -77,6 +88,8 @@ SIGNATURES = [
     ("gpm_estimate", _i32, [_V, P(Pattern), _i32, _dbl, _dbl, _u64, P(Config), P(Result)]),
     ("gpm_estimate_batch", _i32, [_V, _u32, P(Pattern), P(_dbl), _dbl, _u64, P(Config), P(Result)]),
     ("gpm_autotune", _i32, [_V, _u32, P(Pattern), _u64, P(Config)]),
+    ("gpm_hybrid_model", _i32, [_V, P(Pattern), _dbl, _dbl, _u64, P(Config), P(HybridInfo)]),
+    ("gpm_mlp_train", _i32, [_V, _V, _V, _u64, _u32, _u32, C.c_float, _V, _V, P(_dbl)]),
     ("gpm_sample_sums", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), P(Sums)]),
     ("gpm_sample_sums_static", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), P(Sums)]),
     ("gpm_trace", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), _V]),

@@ -35,16 +35,23 @@ def pattern(spec, induced=None):
 def config(**kw):
     cfg = _lib.Config()
     mlp = kw.pop("mlp", None)
+    selector = kw.pop("selector", None)
     for key, val in kw.items():
         if val is None:
             continue
         if key == "verify" and isinstance(val, str):
             val = {"intersect": VERIFY_INTERSECT, "check": VERIFY_CHECK}[val]
         setattr(cfg, key, val)
+    keep = []
     if mlp is not None:
         st = mlp.c_struct()
         cfg.mlp = C.pointer(st)
-        cfg._keep = (mlp, st)
+        keep += [mlp, st]
+    if selector is not None:
+        ss = selector.c_struct()
+        cfg.selector = C.pointer(ss)
+        keep += [selector, ss]
+    cfg._keep = keep
     return cfg
 
 
@@ -116,6 +123,15 @@ class Graph:
         code = L.gpm_estimate_batch(self.h, len(pats), arr, e, delta, seed, C.byref(c), res)
         check(code, "gpm_estimate_batch", (_lib.GPM_OK, _lib.GPM_ERR_NOT_CONVERGED))
         return [r.as_dict() for r in res]
+
+    def hybrid_model(self, pat, eps=0.01, delta=0.01, seed=1, **cfg):
+        """The hybrid choice's inputs and decisions (no engine run)."""
+        info = _lib.HybridInfo()
+        pp = pattern(pat)
+        c = config(**cfg)
+        check(_lib.load().gpm_hybrid_model(self.h, C.byref(pp), eps, delta, seed, C.byref(c), C.byref(info)),
+              "gpm_hybrid_model")
+        return info.as_dict()
 
     def autotune(self, pats, seed=1, **cfg):
         """Fastest launch shape for these patterns: dict(block_warps, cap)."""
@@ -222,6 +238,16 @@ class Proposal:
                                              C.c_void_p(self.w32.data_ptr()), C.c_void_p(self.w16.data_ptr()),
                                              C.byref(loss), C.byref(rows)), "gpm_train_proposal")
         return loss.value, rows.value
+
+    def train_rows(self, graph, feat, label, epochs=200, batch=4096, lr=1e-2):
+        """Adam on given rows (CUDA float tensors feat [n, 3], label [n])."""
+        feat = feat.contiguous().float()
+        label = label.contiguous().float()
+        loss = C.c_double()
+        check(_lib.load().gpm_mlp_train(graph.h, C.c_void_p(feat.data_ptr()), C.c_void_p(label.data_ptr()),
+                                        feat.shape[0], epochs, batch, lr, C.c_void_p(self.w32.data_ptr()),
+                                        C.c_void_p(self.w16.data_ptr()), C.byref(loss)), "gpm_mlp_train")
+        return loss.value
 
     def scores(self, graph, feat):
         """Sampler scores a_x of feature rows (CUDA float tensor [n, 3])."""

@@ -25,6 +25,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <thread>
 
 #include "device.cuh"
 #include "internal.h"
@@ -129,18 +130,12 @@ __device__ __forceinline__ void level_init(const DGraph &g, const Plan &p, const
     __syncwarp();
 }
 
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// budget_ns > 0: every warp stops once budget_ns have passed since it started
-// (checked at each grab of first edges and every 64 search steps) and raises
-// *timed_out; the total is then a lower bound.
+// stop (host memory mapped into the device, or null): once the host sets it,
+// every warp leaves at its next grab of first edges or within 256 search
+// steps and raises *timed_out; the total is then a lower bound.
 __global__ void __launch_bounds__(256) exact_kernel(const DGraph g, const Plan p, uint64_t M, unsigned int *counter,
-                                                    uint32_t per_grab, unsigned long long *total, uint64_t budget_ns,
-                                                    unsigned int *timed_out) {
+                                                    uint32_t per_grab, unsigned long long *total,
+                                                    const volatile int *stop, unsigned int *timed_out) {
     __shared__ Level lev[8][kMaxK];
     __shared__ uint32_t vv[8][kMaxK];
     __shared__ uint32_t buf[8][kMaxK][32];
@@ -149,14 +144,15 @@ __global__ void __launch_bounds__(256) exact_kernel(const DGraph g, const Plan p
     uint32_t *v = vv[warp];
     const int k = p.k;
     unsigned long long acc = 0;
-    const uint64_t t_start = budget_ns ? __shfl_sync(kFull, global_ns(), 0) : 0;
     bool out_of_time = false;
     uint32_t steps = 0;
+    auto stopped = [&]() -> bool {
+        int f = 0;
+        if (lane == 0) f = *stop;
+        return __shfl_sync(kFull, f, 0) != 0;
+    };
     for (;;) {
-        if (budget_ns) {
-            const uint64_t now = __shfl_sync(kFull, global_ns(), 0);
-            if (now - t_start > budget_ns) out_of_time = true;
-        }
+        if (stop && stopped()) out_of_time = true;
         if (out_of_time) break;
         unsigned grab = 0;
         if (lane == 0) grab = atomicAdd(counter, 1u);
@@ -197,12 +193,9 @@ __global__ void __launch_bounds__(256) exact_kernel(const DGraph g, const Plan p
             int j = 2;
             level_init(g, p, v, j, lb, le, &L[j]);
             while (j >= 2) {
-                if (budget_ns && ((++steps) & 63u) == 0) {
-                    const uint64_t now = __shfl_sync(kFull, global_ns(), 0);
-                    if (now - t_start > budget_ns) {
-                        out_of_time = true;
-                        break;
-                    }
+                if (stop && ((++steps) & 255u) == 0 && stopped()) {
+                    out_of_time = true;
+                    break;
                 }
                 Level &cur = L[j];
                 const bool last = (j == k - 1);
@@ -269,15 +262,40 @@ gpm_status exact_count_plan(gpm_graph *h, const Plan &p, uint64_t *out, float *k
     }
     cudaMemsetAsync(tot, 0, sizeof(unsigned long long), h->stream);
     cudaMemsetAsync(ctr, 0, sizeof(unsigned int) * 2, h->stream);
-    const uint64_t budget_ns = max_seconds > 0.0 ? (uint64_t)(max_seconds * 1e9) : 0;
+    // the stop flag lives in pinned host memory mapped into the device
+    int *stop_h = nullptr, *stop_d = nullptr;
+    if (max_seconds > 0.0) {
+        if (cudaHostAlloc((void **)&stop_h, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer((void **)&stop_d, stop_h, 0) != cudaSuccess) {
+            if (stop_h) cudaFreeHost(stop_h);
+            cudaFreeAsync(tot, h->stream);
+            cudaFreeAsync(ctr, h->stream);
+            set_error("exact count: mapped host allocation failed");
+            return GPM_ERR_OOM;
+        }
+        *(volatile int *)stop_h = 0;
+    }
+    const auto t_launch = std::chrono::steady_clock::now();
     uint64_t per = M / ((uint64_t)h->sm_count * 8 * 8 * 64) + 1;
     if (per > 64) per = 64;
     if (M / per >= (1ull << 32)) per = M / (1ull << 31) + 1;
     if (kernel_ms) cudaEventRecord(h->ev0, h->stream);
     if (M > 0)
-        exact_kernel<<<h->sm_count * 8, 256, 0, h->stream>>>(h->d, p, M, ctr, (uint32_t)per, tot, budget_ns, ctr + 1);
+        exact_kernel<<<h->sm_count * 8, 256, 0, h->stream>>>(h->d, p, M, ctr, (uint32_t)per, tot, stop_d, ctr + 1);
     if (kernel_ms) cudaEventRecord(h->ev1, h->stream);
     cudaError_t e = cudaGetLastError();
+    // wall-clock watchdog: raise the flag once max_seconds have passed
+    while (e == cudaSuccess && stop_h) {
+        const cudaError_t q = cudaStreamQuery(h->stream);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) {
+            e = q;
+            break;
+        }
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_launch).count();
+        if (el >= max_seconds) *(volatile int *)stop_h = 1;
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
     unsigned long long r = 0;
     unsigned int late = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&r, tot, sizeof(r), cudaMemcpyDeviceToHost, h->stream);
@@ -285,6 +303,7 @@ gpm_status exact_count_plan(gpm_graph *h, const Plan &p, uint64_t *out, float *k
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFreeAsync(tot, h->stream);
     cudaFreeAsync(ctr, h->stream);
+    if (stop_h) cudaFreeHost(stop_h);
     if (e != cudaSuccess) {
         set_error(std::string("exact count: ") + cudaGetErrorString(e));
         return GPM_ERR_CUDA;

@@ -21,7 +21,7 @@ struct Plan {
     uint32_t back[kMaxK];         // positions i < j adjacent to j in the pattern
     uint32_t nonback[kMaxK];      // positions i < j not adjacent to j
     uint32_t lower[kMaxK];        // positions i < j with the restriction v_i < v_j
-    uint32_t reuse[kMaxK];        // 1: S_j = {x in S_{j-1} : x in N(v_{j-1}), x above the bounds}
+    uint32_t reuse[kMaxK];        // S_j from S_{j-1} above the bounds: 1 keep N(v_{j-1}), 2 drop it, 3 neither
     uint32_t last_back[kMaxK];    // largest back-neighbour position of j
     int32_t res_lo[64], res_hi[64];
 };

@@ -336,6 +336,32 @@ static gpm_status loss_grad(cudaStream_t st, int sms, const float *w, const floa
 
 using namespace gpm;
 
+namespace gpm {
+// Scores of feature rows given on the host (a handful: the selector head).
+gpm_status mlp_score_rows(gpm_graph *h, const gpm_mlp *mlp, const float *feat_host, uint64_t n, uint32_t *out_host) {
+    float *f = nullptr;
+    uint32_t *o = nullptr;
+    if (cudaMalloc((void **)&f, sizeof(float) * 3 * n) != cudaSuccess ||
+        cudaMalloc((void **)&o, sizeof(uint32_t) * n) != cudaSuccess) {
+        cudaFree(f);
+        set_error("selector: device allocation failed");
+        return GPM_ERR_OOM;
+    }
+    gpm_status st = GPM_OK;
+    cudaError_t e = cudaMemcpyAsync(f, feat_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) st = cuda_fail("selector", e);
+    if (st == GPM_OK) st = gpm_mlp_scores(h, mlp, f, n, o);
+    if (st == GPM_OK) {
+        e = cudaMemcpyAsync(out_host, o, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = cuda_fail("selector", e);
+    }
+    cudaFree(f);
+    cudaFree(o);
+    return st;
+}
+}  // namespace gpm
+
 extern "C" gpm_status gpm_mlp_scores(gpm_graph *h, const gpm_mlp *mlp, const float *feat, uint64_t n,
                                      uint32_t *out) {
     if (!h || !mlp || (n && (!feat || !out))) {
@@ -418,6 +444,73 @@ extern "C" gpm_status gpm_proposal_features(gpm_graph *h, const gpm_pattern *pat
     return e == cudaSuccess ? GPM_OK : cuda_fail("gpm_proposal_features", e);
 }
 
+namespace gpm {
+
+// Adam over minibatches of `batch` rows for `epochs` passes, then the loss of
+// the final weights over all rows and their BF16 copy.
+static gpm_status train_rows(gpm_graph *h, const float *feat, const float *label, uint64_t rows, uint32_t epochs,
+                             uint32_t batch, float lr, float *w32, uint16_t *w16, double *final_loss) {
+    cudaStream_t st = h->stream;
+    float *grad = nullptr, *m = nullptr, *v = nullptr, *part = nullptr;
+    double *lpart = nullptr, *d_loss = nullptr;
+    uint32_t cap = 0;
+    auto cleanup = [&]() {
+        cudaFree(grad);
+        cudaFree(m);
+        cudaFree(v);
+        cudaFree(part);
+        cudaFree(lpart);
+        cudaFree(d_loss);
+    };
+    if (cudaMalloc((void **)&grad, sizeof(float) * kGradFloats) != cudaSuccess ||
+        cudaMalloc((void **)&m, sizeof(float) * kGradFloats) != cudaSuccess ||
+        cudaMalloc((void **)&v, sizeof(float) * kGradFloats) != cudaSuccess ||
+        cudaMalloc((void **)&d_loss, sizeof(double)) != cudaSuccess) {
+        cleanup();
+        set_error("mlp training: device allocation failed");
+        return GPM_ERR_OOM;
+    }
+    cudaMemsetAsync(m, 0, sizeof(float) * kGradFloats, st);
+    cudaMemsetAsync(v, 0, sizeof(float) * kGradFloats, st);
+    gpm_status s = GPM_OK;
+    uint64_t step = 0;
+    for (uint32_t ep = 0; ep < epochs && s == GPM_OK; ep++) {
+        for (uint64_t r0 = 0; r0 < rows && s == GPM_OK; r0 += batch) {
+            const uint64_t nr = (r0 + batch < rows) ? batch : rows - r0;
+            s = loss_grad(st, h->sm_count, w32, feat, label, r0, nr, nr, grad, d_loss, &part, &lpart, &cap);
+            if (s != GPM_OK) break;
+            step++;
+            const float c1 = 1.f - powf(0.9f, (float)step), c2 = 1.f - powf(0.999f, (float)step);
+            adam_step<<<(kGradFloats + 255) / 256, 256, 0, st>>>(w32, grad, m, v, lr, 0.9f, 0.999f, 1e-8f, c1, c2, w16);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) s = cuda_fail("adam", e);
+        }
+    }
+    if (s == GPM_OK) {
+        s = loss_grad(st, h->sm_count, w32, feat, label, 0, rows, rows, grad, d_loss, &part, &lpart, &cap);
+        to_bf16<<<(kGradFloats + 255) / 256, 256, 0, st>>>(w32, w16);
+        double lh = 0.0;
+        cudaError_t e = cudaMemcpyAsync(&lh, d_loss, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess && s == GPM_OK) s = cuda_fail("mlp training", e);
+        if (final_loss) *final_loss = lh;
+    }
+    cleanup();
+    return s;
+}
+
+}  // namespace gpm
+
+extern "C" gpm_status gpm_mlp_train(gpm_graph *h, const float *feat, const float *label, uint64_t rows,
+                                    uint32_t epochs, uint32_t batch, float lr, float *w32, uint16_t *w16,
+                                    double *final_loss) {
+    if (!h || !feat || !label || !w32 || !w16 || rows == 0 || epochs == 0 || batch == 0 || !(lr > 0.f)) {
+        set_error("gpm_mlp_train: bad argument");
+        return GPM_ERR_ARG;
+    }
+    return train_rows(h, feat, label, rows, epochs, batch, lr, w32, w16, final_loss);
+}
+
 extern "C" gpm_status gpm_train_proposal(gpm_graph *h, const gpm_pattern *pattern, uint64_t seed, uint64_t samples,
                                          uint32_t epochs, uint32_t batch, float lr, float *w32, uint16_t *w16,
                                          double *final_loss, uint64_t *rows_used) {
@@ -435,30 +528,17 @@ extern "C" gpm_status gpm_train_proposal(gpm_graph *h, const gpm_pattern *patter
         set_error("gpm_train_proposal: the learned proposal acts on steps j <= k-2, so k >= 4");
         return GPM_ERR_ARG;
     }
-    cudaStream_t st = h->stream;
     gpm_sample_record *recs = nullptr;
-    float *feat = nullptr, *label = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *part = nullptr;
-    double *lpart = nullptr, *d_loss = nullptr;
-    uint32_t cap = 0;
+    float *feat = nullptr, *label = nullptr;
     auto cleanup = [&]() {
         cudaFree(recs);
         cudaFree(feat);
         cudaFree(label);
-        cudaFree(grad);
-        cudaFree(m);
-        cudaFree(v);
-        cudaFree(part);
-        cudaFree(lpart);
-        cudaFree(d_loss);
     };
     const uint64_t max_rows = samples * (uint64_t)(p.k - 3);
     if (cudaMalloc((void **)&recs, sizeof(gpm_sample_record) * samples) != cudaSuccess ||
         cudaMalloc((void **)&feat, sizeof(float) * 3 * max_rows) != cudaSuccess ||
-        cudaMalloc((void **)&label, sizeof(float) * max_rows) != cudaSuccess ||
-        cudaMalloc((void **)&grad, sizeof(float) * kGradFloats) != cudaSuccess ||
-        cudaMalloc((void **)&m, sizeof(float) * kGradFloats) != cudaSuccess ||
-        cudaMalloc((void **)&v, sizeof(float) * kGradFloats) != cudaSuccess ||
-        cudaMalloc((void **)&d_loss, sizeof(double)) != cudaSuccess) {
+        cudaMalloc((void **)&label, sizeof(float) * max_rows) != cudaSuccess) {
         cleanup();
         set_error("gpm_train_proposal: device allocation failed");
         return GPM_ERR_OOM;
@@ -472,32 +552,11 @@ extern "C" gpm_status gpm_train_proposal(gpm_graph *h, const gpm_pattern *patter
         s = GPM_ERR_ARG;
         set_error("gpm_train_proposal: no training rows (no sample passed step 2)");
     }
-    cudaMemsetAsync(m, 0, sizeof(float) * kGradFloats, st);
-    cudaMemsetAsync(v, 0, sizeof(float) * kGradFloats, st);
-    uint64_t step = 0;
-    for (uint32_t ep = 0; ep < epochs && s == GPM_OK; ep++) {
-        for (uint64_t r0 = 0; r0 < rows && s == GPM_OK; r0 += batch) {
-            const uint64_t nr = (r0 + batch < rows) ? batch : rows - r0;
-            s = loss_grad(st, h->sm_count, w32, feat, label, r0, nr, nr, grad, d_loss, &part, &lpart, &cap);
-            if (s != GPM_OK) break;
-            step++;
-            const float c1 = 1.f - powf(0.9f, (float)step), c2 = 1.f - powf(0.999f, (float)step);
-            adam_step<<<(kGradFloats + 255) / 256, 256, 0, st>>>(w32, grad, m, v, lr, 0.9f, 0.999f, 1e-8f, c1, c2, w16);
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) s = cuda_fail("adam", e);
-        }
-    }
-    if (s == GPM_OK) {
-        // loss of the final weights over every row
-        s = loss_grad(st, h->sm_count, w32, feat, label, 0, rows, rows, grad, d_loss, &part, &lpart, &cap);
-        to_bf16<<<(kGradFloats + 255) / 256, 256, 0, st>>>(w32, w16);
-        double lh = 0.0;
-        cudaError_t e = cudaMemcpyAsync(&lh, d_loss, sizeof(double), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) s = cuda_fail("gpm_train_proposal", e);
-        if (final_loss) *final_loss = lh;
-        if (rows_used) *rows_used = rows;
-    }
+    // the records are not needed during training
+    cudaFree(recs);
+    recs = nullptr;
+    if (s == GPM_OK) s = train_rows(h, feat, label, rows, epochs, batch, lr, w32, w16, final_loss);
+    if (s == GPM_OK && rows_used) *rows_used = rows;
     cleanup();
     return s;
 }

@@ -420,6 +420,20 @@ struct HybridModel {
     int choose_gs;
 };
 
+gpm_status mlp_score_rows(gpm_graph *h, const gpm_mlp *mlp, const float *feat_host, uint64_t n, uint32_t *out_host);
+
+static float clamp64(double x) {
+    if (!(x == x)) return 0.f;
+    return (float)(x > 64.0 ? 64.0 : (x < -64.0 ? -64.0 : x));
+}
+
+// Selector features: log2(t_gs / t_lo), log2(t_hi / t_lo), log2(n_s).
+static void selector_features(const HybridModel &hm, float f[3]) {
+    f[0] = clamp64(std::log2(hm.t_gs / hm.t_lo));
+    f[1] = clamp64(std::log2(hm.t_hi / hm.t_lo));
+    f[2] = clamp64(std::log2(hm.n_s));
+}
+
 static gpm_status hybrid_model(gpm_graph *h, const Plan &p, double eps, double delta, uint64_t seed,
                                const gpm_config *cfg, HybridModel *hm) {
     const uint64_t Wp = (cfg && cfg->window) ? cfg->window : (1ull << 20);
@@ -499,11 +513,43 @@ static gpm_status hybrid_model(gpm_graph *h, const Plan &p, double eps, double d
     return GPM_OK;
 }
 
+// The decision: the selector head's score (GS iff a >= 2049, i.e. the logit
+// is >= 0) when one is configured, else the cost-model rule.
+static gpm_status hybrid_decide(gpm_graph *h, const Plan &p, double eps, double delta, uint64_t seed,
+                                const gpm_config *cfg, HybridModel *hm, gpm_hybrid_info *info) {
+    gpm_status st = hybrid_model(h, p, eps, delta, seed, cfg, hm);
+    if (st != GPM_OK) return st;
+    float f[3];
+    selector_features(*hm, f);
+    int sel = -1;
+    if (cfg && cfg->selector) {
+        uint32_t a = 0;
+        st = mlp_score_rows(h, cfg->selector, f, 1, &a);
+        if (st != GPM_OK) return st;
+        sel = a >= 2049 ? 1 : 0;
+    }
+    if (info) {
+        info->n_s = hm->n_s;
+        info->t_lo = hm->t_lo;
+        info->t_hi = hm->t_hi;
+        info->t_gs = hm->t_gs;
+        info->t_pre = hm->t_pre;
+        info->t_search = hm->t_search;
+        info->c_step = hm->c_step;
+        info->triangles = hm->triangles;
+        for (int i = 0; i < 3; i++) info->features[i] = f[i];
+        info->cost_model_gs = hm->choose_gs;
+        info->selector_gs = sel;
+    }
+    if (sel >= 0) hm->choose_gs = sel;
+    return GPM_OK;
+}
+
 static gpm_status hybrid_estimate(gpm_graph *h, const Plan &p, double eps, double delta, uint64_t seed,
                                   const gpm_config *cfg, gpm_result *out) {
     const auto t0 = std::chrono::steady_clock::now();
     HybridModel hm;
-    gpm_status st = hybrid_model(h, p, eps, delta, seed, cfg, &hm);
+    gpm_status st = hybrid_decide(h, p, eps, delta, seed, cfg, &hm, nullptr);
     if (st != GPM_OK) return st;
     const double t_pilot = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (hm.choose_gs) st = gs_estimate(h, p, seed, cfg, out);
@@ -515,6 +561,24 @@ static gpm_status hybrid_estimate(gpm_graph *h, const Plan &p, double eps, doubl
 }
 
 }  // namespace gpm
+
+extern "C" gpm_status gpm_hybrid_model(gpm_graph *h, const gpm_pattern *pattern, double eps, double delta,
+                                       uint64_t seed, const gpm_config *cfg, gpm_hybrid_info *out) {
+    if (!h || !out) {
+        set_error("gpm_hybrid_model: null argument");
+        return GPM_ERR_ARG;
+    }
+    if (!(eps > 0.0) || !(delta > 0.0 && delta < 1.0)) {
+        set_error("eps must be > 0 and delta in (0, 1)");
+        return GPM_ERR_ARG;
+    }
+    std::memset(out, 0, sizeof(*out));
+    Plan p;
+    gpm_status st = plan_or_error(pattern, &p);
+    if (st != GPM_OK) return st;
+    HybridModel hm;
+    return hybrid_decide(h, p, eps, delta, seed, cfg, &hm, out);
+}
 
 extern "C" gpm_status gpm_estimate(gpm_graph *h, const gpm_pattern *pattern, gpm_scheme scheme, double eps,
                                    double delta, uint64_t seed, const gpm_config *cfg, gpm_result *out) {

@@ -149,7 +149,10 @@ std::string build_plan(const gpm_pattern &pat, Plan *out) {
         bool same = ((as.adj[j] & below) == (as.adj[j - 1] & below));
         bool links = (as.adj[j] >> (j - 1)) & 1u;
         bool bounds = (out->lower[j] & out->lower[j - 1]) == out->lower[j - 1];
-        out->reuse[j] = (same && links && bounds) ? 1u : 0u;
+        // S_j is S_{j-1} (same adjacency to every earlier position, bounds that
+        // only grow) cut by N(v_{j-1}): kept if adjacent (1), removed if the
+        // count is vertex-induced (2), else only filtered by the bounds (3)
+        if (same && bounds) out->reuse[j] = links ? 1u : (pat.induced ? 2u : 3u);
     }
     return "";
 }

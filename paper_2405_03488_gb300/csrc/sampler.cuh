@@ -187,7 +187,7 @@ static __device__ __noinline__ uint64_t lookahead_count(const DGraph &g, const P
             lo = vi > lo ? vi : lo;
         }
     uint64_t cnt = 0;
-    if (p.reuse[jj]) {
+    if (p.reuse[jj] == 1) {
         uint32_t s0 = 0;
         if (has_lo)
             for (uint32_t base = 0; base < sz; base += 32) {
@@ -410,12 +410,12 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
             uint32_t *Sp = (j & 1) ? wm.S0 : wm.S1;
             uint64_t count = 0;
             bool mat = true;
-            if (p.reuse[j] && prev_mat) {
+            if (p.reuse[j] == 1 && prev_mat) {
                 // S_j = S_{j-1} (on chip) cut by N(v_{j-1}) above the bound
                 const uint64_t b = __shfl_sync(kFull, lb, j - 1);
                 const uint64_t en = __shfl_sync(kFull, le, j - 1);
                 const uint64_t start = above(j - 1, b, en);
-                const uint64_t L = en > start ? en - start : 0;
+                const uint64_t L = en - start;
                 const uint32_t P = prev_size;
                 if (L <= 8ull * P + 32) {
                     for (uint64_t base = start; base < en; base += 128) {
@@ -443,6 +443,24 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                         if (ok) Sc[count + __popc(m & lanemask_lt())] = y;
                         count += __popc(m);
                     }
+                }
+            } else if (p.reuse[j] >= 2 && prev_mat) {
+                // S_j = S_{j-1} (on chip) above the bound, without v_{j-1}, and
+                // (vertex-induced) without N(v_{j-1})
+                const uint64_t b = __shfl_sync(kFull, lb, j - 1);
+                const uint64_t en = __shfl_sync(kFull, le, j - 1);
+                const uint32_t vj1 = wm.v[j - 1];
+                const bool drop = p.reuse[j] == 2;
+                const uint32_t P = prev_size;
+                for (uint32_t base = 0; base < P; base += 32) {
+                    const uint32_t idx = base + lane;
+                    const bool valid = idx < P;
+                    const uint32_t y = valid ? Sp[idx] : 0u;
+                    bool ok = valid && (!has_lo || y > lo) && y != vj1;
+                    if (drop) ok = ok && !lane_contains(g.col + b, en - b, y);
+                    const unsigned m = __ballot_sync(kFull, ok);
+                    if (ok) Sc[count + __popc(m & lanemask_lt())] = y;
+                    count += __popc(m);
                 }
             } else {
                 // driver: shortest back-neighbour list, streamed; partner: the

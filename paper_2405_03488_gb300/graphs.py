@@ -29,33 +29,73 @@ def _gen(seed, device):
     return g
 
 
-def csr_from_edges(src, dst, n, relabel=False):
-    """Symmetrise, drop loops, deduplicate and sort; optional degree relabel."""
-    src = src.to(torch.int64)
-    dst = dst.to(torch.int64)
-    keep = src != dst
-    src, dst = src[keep], dst[keep]
-    s = torch.cat([src, dst])
-    d = torch.cat([dst, src])
-    del src, dst
-    keys = torch.unique(s * n + d)
-    del s, d
+_UNIQUE_LIMIT = 1 << 31
+
+
+def _unique(keys, n):
+    """Sorted unique keys s * n + d; above 2^31 entries (the sort library's
+    size limit) the keys are split at source vertices chosen so that every part
+    holds about the same number of entries, and each part is made unique."""
+    if keys.numel() < _UNIQUE_LIMIT:
+        return torch.unique(keys)
+    parts = 2 * ((keys.numel() + _UNIQUE_LIMIT - 1) // _UNIQUE_LIMIT)
+    per_src = torch.cumsum(torch.bincount(keys // n, minlength=n), 0)
+    targets = torch.arange(1, parts, device=keys.device, dtype=per_src.dtype) * (keys.numel() // parts)
+    cuts = torch.searchsorted(per_src, targets).tolist()
+    bounds = sorted(set([0] + [c * n for c in cuts] + [n * n]))
+    del per_src
+    out = []
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        sel = keys[(keys >= a) & (keys < b)]
+        if sel.numel():
+            out.append(torch.unique(sel))
+        del sel
+    return torch.cat(out)
+
+
+def _csr_from_keys(box, n, relabel):
+    """CSR from directed keys s * n + d (box = [keys], emptied here so that no
+    caller frame keeps the array alive)."""
+    keys = _unique(box.pop(), n)
     if relabel:
         s = keys // n
         deg = torch.bincount(s, minlength=n)
         order = torch.sort(deg, stable=True).indices          # new id -> old id
         newid = torch.empty_like(order)
         newid[order] = torch.arange(n, device=order.device)
-        d = keys % n
-        keys = torch.sort(newid[s] * n + newid[d]).values
-        del s, d, deg, order, newid
+        del deg, order
+        s = newid[s]
+        d = newid[keys % n]
+        del keys, newid
+        s.mul_(n).add_(d)
+        del d
+        keys = _unique(s, n)
+        del s
     s = keys // n
     col = (keys % n).to(torch.int32)
     del keys
     counts = torch.bincount(s, minlength=n)
+    del s
     row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=col.device)
     row_ptr[1:] = torch.cumsum(counts, 0)
     return row_ptr, col
+
+
+def _symmetric_keys(box, n):
+    """box = [src, dst] (emptied): keys of both directions, self-loops dropped."""
+    dst = box.pop().to(torch.int64)
+    src = box.pop().to(torch.int64)
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    del keep
+    keys = torch.cat([src * n + dst, dst * n + src])
+    del src, dst
+    return keys
+
+
+def csr_from_edges(src, dst, n, relabel=False):
+    """Symmetrise, drop loops, deduplicate and sort; optional degree relabel."""
+    return _csr_from_keys([_symmetric_keys([src, dst], n)], n, relabel)
 
 
 def relabel_by_degree(row_ptr, col):
@@ -103,7 +143,11 @@ def rmat(scale, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=2, device="cpu", re
         perm = torch.randperm(n, generator=g, device=device)
         src = perm[src]
         dst = perm[dst]
-    return csr_from_edges(src, dst, n, relabel=relabel)
+        del perm
+    box = [src, dst]
+    del src, dst
+    box = [_symmetric_keys(box, n)]
+    return _csr_from_keys(box, n, relabel)
 
 
 def chung_lu(n, gamma=2.1, mean_degree=20.0, n_cliques=200, clique_size=12, seed=4,

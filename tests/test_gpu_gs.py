@@ -104,3 +104,32 @@ def test_exact_count_deadline_returns_a_lower_bound():
     # a small case finishes inside the budget and is exact
     r = g.estimate("triangle", scheme=api.EXACT, max_seconds=30.0)
     assert r["converged"] == 1 and r["exact_count"] == math.comb(200, 3)
+
+
+def test_selector_head_decides_the_hybrid():
+    """A selector head trained on a few cases decides the hybrid's choice from
+    the features of that very call, and the hybrid returns that engine's result."""
+    import torch
+    rp, col = G.erdos_renyi(3000, 0.01, seed=4)
+    g = api.Graph(rp.cuda(), col.cuda())
+    feats, labels = [], []
+    for name in ("triangle", "4-clique", "4-cycle", "house"):
+        info = g.hybrid_model(name, eps=0.05, delta=0.01, seed=3, window=1 << 15)
+        assert len(info["features"]) == 3 and info["selector_gs"] == -1
+        assert info["cost_model_gs"] in (0, 1) and info["t_lo"] <= info["t_hi"]
+        feats.append(info["features"])
+        labels.append(float(info["cost_model_gs"] == 0))   # train the head to disagree with the cost model
+    sel = api.Proposal(seed=5)
+    loss = sel.train_rows(g, torch.tensor(feats).cuda(), torch.tensor(labels).cuda(), epochs=500, batch=8, lr=2e-2)
+    assert np.isfinite(loss)
+    for name in ("triangle", "4-clique", "4-cycle", "house"):
+        # the features include measured times, so compare against this call's own features
+        info = g.hybrid_model(name, eps=0.05, delta=0.01, seed=3, window=1 << 15, selector=sel)
+        want = int(sel.scores(g, torch.tensor([info["features"]]).cuda())[0].item() >= 2049)
+        assert info["selector_gs"] == want
+        r = g.estimate(name, scheme=api.HYBRID, eps=0.05, delta=0.01, seed=3, window=1 << 15, selector=sel)
+        assert r["scheme_used"] in (api.NS, api.GS)
+        if r["scheme_used"] == api.GS:
+            assert r["estimate"] == g.estimate(name, scheme=api.GS, seed=3)["estimate"]
+        else:
+            assert r["converged"] == 1
