@@ -307,20 +307,27 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_ctl, &ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
     uint32_t blocks = 0;
+    bool single = false;
+    for (const Plan &pl : plans) single = single || plan_single_steps(pl);
+    const int kmode = kernel_mode(mode, single);
     if (e == cudaSuccess)
-        e = (mode == MODE_CHECK)     ? batch_grid<MODE_CHECK>(h, sh, &blocks)
-            : (mode == MODE_LEARNED) ? batch_grid<MODE_LEARNED>(h, sh, &blocks)
-                                     : batch_grid<MODE_INTERSECT>(h, sh, &blocks);
+        e = (kmode == MODE_CHECK)              ? batch_grid<MODE_CHECK>(h, sh, &blocks)
+            : (kmode == MODE_LEARNED)          ? batch_grid<MODE_LEARNED>(h, sh, &blocks)
+            : (kmode == MODE_INTERSECT_SINGLE) ? batch_grid<MODE_INTERSECT_SINGLE>(h, sh, &blocks)
+                                               : batch_grid<MODE_INTERSECT>(h, sh, &blocks);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         const size_t smem = smem_bytes(sh, mode);
         for (int r = 0; r < R; r++) {
             // event nodes around each sampler launch time the sampler alone
             cudaEventRecordWithFlags(ev_k[2 * r], cs, cudaEventRecordExternal);
-            if (mode == MODE_CHECK)
+            if (kmode == MODE_CHECK)
                 ns_batch_kernel<MODE_CHECK><<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
-            else if (mode == MODE_LEARNED)
+            else if (kmode == MODE_LEARNED)
                 ns_batch_kernel<MODE_LEARNED>
+                    <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
+            else if (kmode == MODE_INTERSECT_SINGLE)
+                ns_batch_kernel<MODE_INTERSECT_SINGLE>
                     <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
             else
                 ns_batch_kernel<MODE_INTERSECT>

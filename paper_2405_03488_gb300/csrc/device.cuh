@@ -80,6 +80,20 @@ __device__ __forceinline__ bool lane_contains(const uint32_t *__restrict__ a, ui
     return __ldg(b) == x;
 }
 
+// Position of x in the sorted global list a[0, len), or ~0 when absent (one
+// lane, the same halving search as lane_contains).
+__device__ __forceinline__ uint64_t lane_find(const uint32_t *__restrict__ a, uint64_t len, uint32_t x) {
+    if (len == 0) return ~0ull;
+    const uint32_t *b = a;
+    uint64_t n = len;
+    while (n > 1) {
+        const uint64_t half = n >> 1;
+        b = (__ldg(b + half) <= x) ? b + half : b;
+        n -= half;
+    }
+    return __ldg(b) == x ? (uint64_t)(b - a) : ~0ull;
+}
+
 // Same on a shared-memory list.
 __device__ __forceinline__ bool lane_contains_shared(const uint32_t *a, uint32_t len, uint32_t x) {
     if (len == 0) return false;

@@ -220,6 +220,9 @@ static gpm_status run_block(gpm_graph *h, const Plan &p, int mode, uint64_t seed
         e = trace ? launch_ns<MODE_CHECK, true>(h, p, sh, a) : launch_ns<MODE_CHECK, false>(h, p, sh, a);
     else if (mode == MODE_LEARNED)
         e = trace ? launch_ns<MODE_LEARNED, true>(h, p, sh, a) : launch_ns<MODE_LEARNED, false>(h, p, sh, a);
+    else if (kernel_mode(mode, plan_single_steps(p)) == MODE_INTERSECT_SINGLE)
+        e = trace ? launch_ns<MODE_INTERSECT_SINGLE, true>(h, p, sh, a)
+                  : launch_ns<MODE_INTERSECT_SINGLE, false>(h, p, sh, a);
     else
         e = trace ? launch_ns<MODE_INTERSECT, true>(h, p, sh, a) : launch_ns<MODE_INTERSECT, false>(h, p, sh, a);
     if (kernel_ms) cudaEventRecord(h->ev1, h->stream);
@@ -715,6 +718,7 @@ extern "C" gpm_status gpm_sample_sums_static(gpm_graph *h, const gpm_pattern *pa
     if (e == cudaSuccess)
         e = (mode == MODE_CHECK)     ? launch_ns<MODE_CHECK, false>(h, p, sh, a)
             : (mode == MODE_LEARNED) ? launch_ns<MODE_LEARNED, false>(h, p, sh, a)
+            : plan_single_steps(p)   ? launch_ns<MODE_INTERSECT_SINGLE, false>(h, p, sh, a)
                                      : launch_ns<MODE_INTERSECT, false>(h, p, sh, a);
     if (e == cudaSuccess) {
         reduce_partials<<<1, 1024, 0, h->stream>>>(parts, (uint32_t)nchunks, tot, 0);

@@ -10,7 +10,10 @@
 
 namespace gpm {
 
-enum { MODE_INTERSECT = 0, MODE_CHECK = 1, MODE_LEARNED = 2 };
+enum { MODE_INTERSECT = 0, MODE_CHECK = 1, MODE_LEARNED = 2, MODE_INTERSECT_SINGLE = 3 };
+// MODE_INTERSECT_SINGLE is MODE_INTERSECT compiled with the position form of
+// single-list steps (below); plans without such steps run the plain variant,
+// whose code stays as small as before.
 
 // resident 256-thread blocks per SM the plain sampler kernels are compiled for
 #ifndef GPM_MIN_BLOCKS
@@ -410,7 +413,32 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
             uint32_t *Sp = (j & 1) ? wm.S0 : wm.S1;
             uint64_t count = 0;
             bool mat = true;
-            if (p.reuse[j] == 1 && prev_mat) {
+            const uint32_t back = p.back[j];
+            if ((MODE == MODE_INTERSECT_SINGLE || (MODE == MODE_LEARNED && j == k - 1)) && !p.induced &&
+                (back & (back - 1)) == 0) {
+                // one back-neighbour v_d, edge-induced: S_j is N(v_d) above the
+                // bound without the matched vertices it holds, so |S_j| and its
+                // t-th element follow from their positions in the list alone
+                const int d = __ffs(back) - 1;
+                const uint64_t db = __shfl_sync(kFull, lb, d);
+                const uint64_t de = __shfl_sync(kFull, le, d);
+                const uint64_t dstart = above(d, db, de);
+                const uint64_t L = de - dstart;
+                const uint64_t q = ((int)lane < j && (int)lane != d) ? lane_find(g.col + dstart, L, wm.v[lane]) : ~0ull;
+                count = L - (uint64_t)__popc(__ballot_sync(kFull, q != ~0ull));
+                if (count) {
+                    // smallest list index with t kept entries before it
+                    const uint64_t t = index_map(r, count);
+                    uint64_t idx = t;
+                    for (;;) {
+                        const uint64_t nx = t + (uint64_t)__popc(__ballot_sync(kFull, q <= idx));
+                        if (nx == idx) break;
+                        idx = nx;
+                    }
+                    x = __ldg(g.col + dstart + idx);
+                }
+                mat = false;
+            } else if (p.reuse[j] == 1 && prev_mat) {
                 // S_j = S_{j-1} (on chip) cut by N(v_{j-1}) above the bound
                 const uint64_t b = __shfl_sync(kFull, lb, j - 1);
                 const uint64_t en = __shfl_sync(kFull, le, j - 1);
@@ -465,7 +493,6 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
             } else {
                 // driver: shortest back-neighbour list, streamed; partner: the
                 // next shortest, staged on chip when its part above the bound fits
-                const uint32_t back = p.back[j];
                 const bool isback = (int)lane < j && ((back >> lane) & 1u);
                 const uint64_t key = isback ? (((le - lb) << 5) | lane) : ~0ull;
                 const int driver = (int)(warp_min_u64(key) & 31u);
@@ -619,6 +646,20 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
     out.wu = (MODE == MODE_LEARNED || ovf) ? 0 : wu;
     out.overflow = ovf;
     return out;
+}
+
+// True when some step of an edge-induced plan has one back-neighbour, the
+// steps the MODE_INTERSECT_SINGLE variant evaluates by list positions.
+inline bool plan_single_steps(const Plan &p) {
+    if (p.induced) return false;
+    for (int j = 2; j < p.k; j++)
+        if ((p.back[j] & (p.back[j] - 1u)) == 0) return true;
+    return false;
+}
+
+// The sampler variant a mode runs with for a plan (or a batch of plans).
+inline int kernel_mode(int mode, bool single) {
+    return (mode == MODE_INTERSECT && single) ? MODE_INTERSECT_SINGLE : mode;
 }
 
 // ------------------------------------------------------------------ launch shape

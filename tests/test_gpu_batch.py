@@ -94,3 +94,24 @@ def test_autotune_returns_a_valid_shape(rmat14):
     assert best["block_warps"] in (2, 4, 8) and best["cap"] in (256, 512, 1024)
     r = g.estimate("4-clique", eps=0.05, seed=1, window=1 << 14, **best)
     assert r["converged"] == 1
+
+
+def test_mixed_batch_runs_single_list_variant_bit_exact(rmat14):
+    """A batch with edge-induced paths and cycles runs the sampler variant that
+    evaluates one-list steps by positions; every job, the cliques included,
+    still equals its separate run and the oracle."""
+    rp, col = rmat14
+    g = api.Graph(rp.cuda(), col.cuda())
+    og = O.Graph(*G.to_numpy(rp, col))
+    names = ["4-clique", "4-cycle", "5-path", "house", "wedge", "5-clique"]
+    W = 1 << 14
+    res = g.estimate_batch(names, [0.02] * len(names), seed=4, window=W, n_max=1 << 22)
+    for q, nm in enumerate(names):
+        single = g.estimate(nm, eps=0.02, seed=4, window=W, n_max=1 << 22, slot=q)
+        for f in FIELDS:
+            assert res[q][f] == single[f], (nm, f)
+    for q in (1, 2):
+        k, edges = G.pattern(names[q])
+        o = O.ns_online(og, O.plan(k, edges, False), 0.02, 0.01, seed=4, window=W, n_max=1 << 22, slot=q)
+        assert res[q]["samples"] == o.samples and res[q]["hits"] == o.hits
+        assert res[q]["estimate"] == pytest.approx(o.estimate, rel=REL)

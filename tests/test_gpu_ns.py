@@ -41,7 +41,9 @@ def assert_same_records(gpu, cpu, k):
 
 PATTERNS = [("triangle", False), ("4-clique", False), ("5-clique", False), ("4-cycle", False),
             ("4-cycle", True), ("diamond", False), ("tailed-triangle", True), ("3-star", True),
-            ("4-path", False), ("house", False), ("5-path", True), ("edge", False)]
+            ("4-path", False), ("house", False), ("5-path", True), ("edge", False),
+            ("5-path", False), ("3-star", False), ("dumbbell", False), ("tailed-triangle", False),
+            ("wedge", False)]
 
 
 @pytest.mark.parametrize("verify", ["intersect", "check"])
@@ -155,7 +157,7 @@ def rmat22():
     return rp, col
 
 
-@pytest.mark.parametrize("name", ["4-clique", "5-clique"])
+@pytest.mark.parametrize("name", ["4-clique", "5-clique", "house", "4-cycle"])
 def test_rmat22_sampled_parity_in_bench_shape(rmat22, name):
     """R-MAT scale 22 (the benchmark workload): records of sample ranges deep
     into a run are bit-exact, in the launch shape the benchmark uses."""
