@@ -21,6 +21,15 @@ enum { MODE_INTERSECT = 0, MODE_CHECK = 1, MODE_LEARNED = 2, MODE_INTERSECT_SING
 #endif
 
 constexpr uint32_t kLearnedMax = 256;   // larger candidate sets are drawn uniformly
+// S_j = S_{j-1} cut by N(v_{j-1}): stream the list through on-chip searches
+// while |list| <= FACTOR * |usable part of S_{j-1}| + BIAS, else search the
+// list for each element of S_{j-1}
+#ifndef GPM_REUSE_STREAM_FACTOR
+#define GPM_REUSE_STREAM_FACTOR 4
+#endif
+#ifndef GPM_REUSE_STREAM_BIAS
+#define GPM_REUSE_STREAM_BIAS 0
+#endif
 constexpr int kMlpFloats = 4481;        // 3->64->64->1 weights and biases
 constexpr int kMlpSmemFloats = 4482;    // padded to 8 bytes
 constexpr int kLearnedWarpWords = 128 + kLearnedMax;   // hidden activations + scores
@@ -358,6 +367,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
     uint64_t wu = M;
     bool ovf = false;
     uint32_t prev_size = 0;
+    uint32_t prev_off = 0;   // 1 + index of v_{j-1} in the on-chip S_{j-1} (0: unknown)
     bool prev_mat = false;
 
     for (int j = 2; j < k; j++) {
@@ -380,6 +390,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
         };
         uint64_t size = 0;
         uint32_t x = 0;
+        uint32_t pick = 0;   // 1 + index of x in the on-chip S_j (0: not drawn from it)
         bool learned_step = false;
         double lfac = 1.0;
         if (MODE == MODE_CHECK) {
@@ -439,13 +450,16 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 }
                 mat = false;
             } else if (p.reuse[j] == 1 && prev_mat) {
-                // S_j = S_{j-1} (on chip) cut by N(v_{j-1}) above the bound
+                // S_j = S_{j-1} (on chip) cut by N(v_{j-1}) above the bound;
+                // when the bound is at least v_{j-1}, only the part of S_{j-1}
+                // after v_{j-1} can qualify
                 const uint64_t b = __shfl_sync(kFull, lb, j - 1);
                 const uint64_t en = __shfl_sync(kFull, le, j - 1);
                 const uint64_t start = above(j - 1, b, en);
                 const uint64_t L = en - start;
+                const uint32_t off = (has_lo && lo >= wm.v[j - 1]) ? prev_off : 0u;
                 const uint32_t P = prev_size;
-                if (L <= 8ull * P + 32) {
+                if (L <= (uint64_t)GPM_REUSE_STREAM_FACTOR * (P - off) + GPM_REUSE_STREAM_BIAS) {
                     for (uint64_t base = start; base < en; base += 128) {
                         uint32_t y[4];
 #pragma unroll
@@ -455,14 +469,14 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                         }
 #pragma unroll
                         for (int u = 0; u < 4; u++) {
-                            const bool ok = (base + 32 * u + lane < en) && lane_contains_shared(Sp, P, y[u]);
+                            const bool ok = (base + 32 * u + lane < en) && lane_contains_shared(Sp + off, P - off, y[u]);
                             const unsigned m = __ballot_sync(kFull, ok);
                             if (ok) Sc[count + __popc(m & lanemask_lt())] = y[u];
                             count += __popc(m);
                         }
                     }
                 } else {
-                    for (uint32_t base = 0; base < P; base += 32) {
+                    for (uint32_t base = off; base < P; base += 32) {
                         const uint32_t idx = base + lane;
                         const bool valid = idx < P;
                         const uint32_t y = valid ? Sp[idx] : 0u;
@@ -480,7 +494,8 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 const uint32_t vj1 = wm.v[j - 1];
                 const bool drop = p.reuse[j] == 2;
                 const uint32_t P = prev_size;
-                for (uint32_t base = 0; base < P; base += 32) {
+                const uint32_t off = (has_lo && lo >= vj1) ? prev_off : 0u;
+                for (uint32_t base = off; base < P; base += 32) {
                     const uint32_t idx = base + lane;
                     const bool valid = idx < P;
                     const uint32_t y = valid ? Sp[idx] : 0u;
@@ -617,9 +632,12 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 lfac = __ddiv_rn((double)A, (double)ax);
                 learned_step = true;
             } else if (mat) {
-                x = Sc[index_map(r, size)];
+                const uint32_t t = (uint32_t)index_map(r, size);
+                x = Sc[t];
+                pick = t + 1;
             }
             prev_size = (uint32_t)(mat ? size : 0);
+            prev_off = pick;
             prev_mat = mat;
         }
         if (lane == 0) wm.v[j] = x;
