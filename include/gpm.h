@@ -88,7 +88,9 @@ typedef struct {
     uint32_t verify;        /* gpm_verify (default INTERSECT) */
     uint32_t grid_blocks;   /* sampler launch shape overrides (0 = tuned default) */
     uint32_t block_warps;
-    uint32_t cap;           /* per-warp on-chip candidate buffer, entries (0 = default) */
+    uint32_t cap;           /* per-warp on-chip candidate buffer, entries (0 = the largest
+                               that keeps 4 resident 256-thread blocks per SM, 2 with a
+                               learned proposal; 832 at 8 warps on a GB300) */
     const gpm_mlp *mlp;     /* learned proposal weights (device); required by GPM_NS_LEARNED and,
                                when set, selects the learned proposal in gpm_sample_sums,
                                gpm_sample_sums_static and gpm_trace */
@@ -199,8 +201,9 @@ gpm_status gpm_estimate_batch(gpm_graph *g, uint32_t count, const gpm_pattern *p
                               gpm_result *out);
 
 /* Times one convergence round of the batch under each candidate launch shape
- * (2, 4 or 8 warps per block; on-chip candidate buffers of 256, 512 or 1024
- * entries per warp) and writes the fastest into io->block_warps and io->cap.
+ * (4 or 8 warps per block; on-chip candidate buffers of 256 or 512 entries per
+ * warp, or the largest that keeps 4 blocks resident per SM) and writes the
+ * fastest into io->block_warps and io->cap.
  * Estimates do not depend on the shape: samples are grouped in fixed chunks of
  * 64 whose partials are reduced in chunk order. */
 gpm_status gpm_autotune(gpm_graph *g, uint32_t count, const gpm_pattern *patterns, uint64_t seed, gpm_config *io);

@@ -48,6 +48,9 @@ struct BatchArgs {
     gpm_mlp mlp;
 };
 
+// static shared memory of ns_batch_kernel: one StepPlan per warp
+constexpr size_t kBatchStaticSmem = 8 * sizeof(StepPlan);
+
 template <int MODE>
 __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOCKS)
     ns_batch_kernel(const DGraph g, const Plan *__restrict__ plans, const BatchJob *jobs, BatchCtl *ctl,
@@ -228,6 +231,10 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
             return GPM_ERR_ARG;
         }
     Shape sh = pick_shape(h, cfg, W);
+    bool single = false;
+    for (const Plan &pl : plans) single = single || plan_single_steps(pl);
+    const int kmode = kernel_mode(mode, single);
+    if (sh.cap == 0) sh.cap = fit_cap(h, kBatchStaticSmem, sh.warps, mode);
     if (mode == MODE_LEARNED && sh.cap < kLearnedMax) sh.cap = kLearnedMax;
     const uint64_t cpj = (W + sh.chunk - 1) / sh.chunk;
     if (cpj * nj >= (1ull << 31)) {
@@ -307,9 +314,6 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_ctl, &ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
     uint32_t blocks = 0;
-    bool single = false;
-    for (const Plan &pl : plans) single = single || plan_single_steps(pl);
-    const int kmode = kernel_mode(mode, single);
     if (e == cudaSuccess)
         e = (kmode == MODE_CHECK)              ? batch_grid<MODE_CHECK>(h, sh, &blocks)
             : (kmode == MODE_LEARNED)          ? batch_grid<MODE_LEARNED>(h, sh, &blocks)
@@ -452,8 +456,9 @@ extern "C" gpm_status gpm_autotune(gpm_graph *h, uint32_t count, const gpm_patte
             return GPM_ERR_ARG;
         }
     }
-    static const uint32_t kWarps[] = {2, 4, 8};
-    static const uint32_t kCaps[] = {256, 512, 1024};
+    // cap 0 = fit_cap, the largest buffer at full residency
+    static const uint32_t kWarps[] = {4, 8};
+    static const uint32_t kCaps[] = {256, 512, 0};
     std::vector<double> eps(count, 1e-300);
     std::vector<gpm_result> res(count);
     double best = INFINITY;
@@ -478,7 +483,7 @@ extern "C" gpm_status gpm_autotune(gpm_graph *h, uint32_t count, const gpm_patte
         }
     }
     io->block_warps = bw;
-    io->cap = bc;
+    io->cap = bc ? bc : fit_cap(h, kBatchStaticSmem, bw, MODE_INTERSECT);
     set_error("");
     return GPM_OK;
 }

@@ -85,5 +85,7 @@ struct gpm_graph {
     unsigned int *counter;        // device chunk counter
     volatile int abort_flag;
     int sm_count;
+    int smem_per_sm;              // shared memory per SM and reserved per block, bytes
+    int smem_reserved;
     cudaEvent_t ev0, ev1;
 };

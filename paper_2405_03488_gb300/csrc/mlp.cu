@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) mlp_fwd_bwd(const float *__restrict__ w, 
                                                    uint32_t rows_per_block, double inv_total, float *part,
                                                    double *loss_part) {
     extern __shared__ float sW[];   // kGradFloats weights
-    __shared__ float sX[kTile * 3], sY[kTile], sZ[kTile], sDz[kTile];
+    __shared__ float sX[kTile * 3], sY[kTile], sDz[kTile];
     __shared__ float sH1[kTile][65];
     __shared__ float sA2[kTile][65];
     __shared__ float gw1[192], gb1[64], gb2[64], gw3[64], gb3s;
@@ -149,7 +149,6 @@ __global__ void __launch_bounds__(256) mlp_fwd_bwd(const float *__restrict__ w, 
                 for (int o = 16; o; o >>= 1) part_z += __shfl_xor_sync(kFull, part_z, o);
                 if (ln == 0) {
                     const float z = part_z + sW[kB3];
-                    sZ[r] = z;
                     if (r < nr) {
                         const double zd = z, y = sY[r];
                         loss += (zd > 0 ? zd : 0.0) - y * zd + log1p(exp(-fabs(zd)));

@@ -91,7 +91,8 @@ def test_autotune_returns_a_valid_shape(rmat14):
     rp, col = rmat14
     g = api.Graph(rp.cuda(), col.cuda())
     best = g.autotune(["4-clique", "5-clique"], window=1 << 14)
-    assert best["block_warps"] in (2, 4, 8) and best["cap"] in (256, 512, 1024)
+    assert best["block_warps"] in (4, 8)
+    assert best["cap"] in (256, 512) or (best["cap"] >= 512 and best["cap"] % 32 == 0)
     r = g.estimate("4-clique", eps=0.05, seed=1, window=1 << 14, **best)
     assert r["converged"] == 1
 
