@@ -47,7 +47,11 @@ typedef enum {
 
 typedef enum {
     GPM_NS = 0,          /* neighbour sampling with eager verify (Sec. 4.1-4.2) */
-    GPM_GS = 1,          /* colour sparsification + exact count (Sec. 2.2.2, 5.2) */
+    GPM_GS = 1,          /* graph sparsification + exact count (Sec. 2.2.2, 5.2; Algorithm 2):
+                            colour classes (cfg->colors) or Bernoulli edges (cfg->edge_p);
+                            cfg->samplers >= 2 independent sparsifications are averaged and
+                            give ci_half_width = z s / sqrt(R), s the sample standard
+                            deviation of the R scaled counts, eps_hat = ci / estimate */
     GPM_HYBRID = 2,      /* cost-model choice between NS and GS (Sec. 4.3-4.4, 5.1) */
     GPM_NS_LEARNED = 3,  /* NS with the learned, importance-weighted proposal */
     GPM_EXACT = 4        /* exact count on the full graph */
@@ -96,6 +100,11 @@ typedef struct {
                                gpm_sample_sums_static and gpm_trace */
     const gpm_mlp *selector; /* GPM_HYBRID: learned NS/GS selector head (device weights, same
                                MLP shape); NULL = the cost-model rule decides */
+    double edge_p;          /* GS: 0 = colour sparsification with `colors`; in (0, 1] =
+                               Bernoulli edge sparsification keeping each edge with this
+                               probability (Algorithm 2; edge-induced patterns only) */
+    uint32_t samplers;      /* GS: independent sparsifications averaged (default 1) */
+    uint32_t pad_;
 } gpm_config;
 
 /* What the hybrid choice saw (Sec. 4.3-4.4, 5.1): the pilot's sample count
@@ -142,6 +151,22 @@ typedef struct {
     uint64_t n, hits;
     double sum, sumsq;
 } gpm_sums;
+
+/* Totals of one 64-sample chunk (the unit every reduction adds in chunk
+ * order). */
+typedef struct {
+    double sum, sumsq;
+    uint64_t hits, n;
+} gpm_partial;
+
+/* Running state of Algorithm 3 for one estimate: totals over the finished
+ * windows and the outcome of the last window test. */
+typedef struct {
+    double sum, sumsq;            /* running totals of X and X^2 */
+    uint64_t hits, n, rounds;
+    double mu, half, eps_hat;     /* estimate, z sigma, z sigma / mu */
+    uint32_t converged, active;   /* start a run with active = 1, everything else 0 */
+} gpm_window;
 
 /* Load a graph (Sec. 6: symmetric CSR without loops or duplicates).
  *  n        vertex count (< 2^32 - 1)
@@ -212,6 +237,40 @@ gpm_status gpm_autotune(gpm_graph *g, uint32_t count, const gpm_pattern *pattern
  * totals of X_i and X_i^2 in FP64.  cfg selects verify mode, slot and MLP. */
 gpm_status gpm_sample_sums(gpm_graph *g, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
                            uint64_t count, const gpm_config *cfg, gpm_sums *out);
+
+/* The per-chunk partials of samples [first, first + count) (Algorithm 3's inner
+ * loop) that fall to one of `world` ranks when the range's 64-sample chunks are
+ * dealt round robin: chunk c (samples first + 64c .. first + 64c + 63, the last
+ * chunk possibly shorter) belongs to rank c mod world.  out[i] receives the
+ * partial of chunk rank + i * world, for every such chunk in the range;
+ * *n_out receives their number, ceil((ceil(count / 64) - rank) / world) when
+ * positive, else 0.  out is a host array with room for that many entries.
+ * Interleaving the ranks' arrays restores chunk order, and gpm_merge_partials
+ * over it gives gpm_sample_sums's totals bit for bit (the multi-GPU form of a
+ * round: each rank samples its chunks, the partials are gathered and merged
+ * in chunk order).  rank < world, world >= 1; cfg selects verify mode, slot
+ * and MLP as for gpm_sample_sums. */
+gpm_status gpm_sample_partials(gpm_graph *g, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
+                               uint64_t count, uint32_t rank, uint32_t world, const gpm_config *cfg,
+                               gpm_partial *out, uint64_t *n_out);
+
+/* Host-only: adds n chunk partials (in chunk order) with the fixed-shape
+ * reduction the device uses for a round -- 1024 contiguous runs of
+ * ceil(n / 1024) partials, each added left to right, then a pairwise tree over
+ * the runs (run t += run t + h for h = 512, 256, ..., 1) -- so the result is
+ * bit-identical to the device's.  n < 2^32.  Needs no GPU. */
+gpm_status gpm_merge_partials(const gpm_partial *parts, uint64_t n, gpm_sums *out);
+
+/* Host-only: one window of Algorithm 3 (Eq. equ:error).  Folds the window's
+ * totals into w (the first window is assigned, later ones added), then with
+ * nn = n: mu = sum / nn, var = max(sumsq / nn - mu^2, 0), sigma = sqrt(var / nn),
+ * half = z sigma, eps_hat = z sigma / mu (infinity unless mu > 0); converged
+ * when n >= n_min, mu > 0 and eps_hat <= eps, else inactive once n >= n_max.
+ * Every step is one correctly rounded FP64 operation in this order, as in the
+ * device's window test, so both decide alike.  z = Phi^-1(1 - delta / 2)
+ * (gpm_normal_quantile).  Needs no GPU. */
+gpm_status gpm_window_update(gpm_window *w, const gpm_sums *window, double z, double eps, uint64_t n_min,
+                             uint64_t n_max);
 
 /* Same result as gpm_sample_sums, for callers that must not allocate device
  * memory during the call.  The paper has no counterpart: this is a library
@@ -286,6 +345,14 @@ gpm_status gpm_train_proposal(gpm_graph *g, const gpm_pattern *pattern, uint64_t
  * col_out (capacity 2m); *kept receives its entry count. */
 gpm_status gpm_sparsify(gpm_graph *g, uint32_t colors, uint64_t seed, uint32_t colouring, uint32_t slot,
                         uint64_t *row_out, uint32_t *col_out, uint64_t *kept);
+
+/* Bernoulli edge sparsification (Algorithm 2): keep probability p realised as
+ * t / 2^32 with t = floor(p * 2^32) (t = 2^32 for p >= 1); edge {u, w} stays
+ * iff the first word of Philox4x32-10 at counter (min(u, w), max(u, w),
+ * colouring, slot << 8 | 3), key = seed, is below t, one decision for both
+ * CSR entries.  Output as gpm_sparsify.  0 < p; t must be positive. */
+gpm_status gpm_sparsify_edges(gpm_graph *g, double p, uint64_t seed, uint32_t colouring, uint32_t slot,
+                              uint64_t *row_out, uint32_t *col_out, uint64_t *kept);
 
 /* Ask a running estimate on this handle to stop at its next round boundary
  * (it returns GPM_ERR_ABORTED with the partial result). */

@@ -20,6 +20,12 @@
  *     with k vertices survives with probability c^-(k-1) (the paper writes the
  *     exponent with the edge count l; for a connected pattern the survival
  *     event is "all k vertices share one colour", so the exponent is k-1).
+ *   - Sec. 2.2.2 / Algorithm 2: Bernoulli edge sparsification keeps every edge
+ *     independently with probability p; a match with l edges survives with
+ *     probability p^l, so the exact count of G' scaled by p^-l is unbiased
+ *     (edge-induced counting; removing edges can create vertex-induced
+ *     occurrences, so that case has no such estimator).  Several independent
+ *     sparsifications ("samplers", Sec. 2.2.2) are averaged.
  *   - Sec. 6 (evaluation setup): vertex-induced (motif) counting uses set
  *     difference for pattern non-edges.
  *
@@ -819,6 +825,43 @@ uint64_t og_sparsify(const og_graph *g, const uint32_t *colors, uint64_t *row_ou
         for (uint64_t i = g->row_ptr[v]; i < g->row_ptr[v + 1]; i++) {
             uint32_t x = g->col[i];
             if (colors[v] == colors[x]) col_out[k++] = x;
+        }
+        row_out[v + 1] = k;
+    }
+    return k;
+}
+
+/* Bernoulli edge sparsification (Algorithm 2).  The keep probability p is
+ * realised as t / 2^32 with t = floor(p * 2^32) (t = 2^32 for p >= 1): edge
+ * {u, w} stays iff the first word of Philox4x32-10 at counter (min(u, w),
+ * max(u, w), colouring, slot << 8 | 3), key = seed, is below t, so both CSR
+ * entries of an edge get one decision. */
+uint64_t og_bes_threshold(double p)
+{
+    if (p >= 1.0) return 1ull << 32;
+    return (uint64_t)floor(p * 4294967296.0);
+}
+
+int og_bes_keep(uint64_t seed, uint32_t u, uint32_t w, uint32_t colouring, uint32_t slot, uint64_t t)
+{
+    uint32_t lo = u < w ? u : w, hi = u < w ? w : u;
+    uint32_t ctr[4] = {lo, hi, colouring, (slot << 8) | 3u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t o[4];
+    og_philox4x32_10(ctr, key, o);
+    return (uint64_t)o[0] < t;
+}
+
+/* The kept CSR of one Bernoulli sparsification; same layout as og_sparsify. */
+uint64_t og_bes_sparsify(const og_graph *g, uint64_t seed, uint32_t colouring, uint32_t slot, uint64_t t,
+                         uint64_t *row_out, uint32_t *col_out)
+{
+    uint64_t k = 0;
+    row_out[0] = 0;
+    for (uint64_t v = 0; v < g->n; v++) {
+        for (uint64_t i = g->row_ptr[v]; i < g->row_ptr[v + 1]; i++) {
+            uint32_t x = g->col[i];
+            if (og_bes_keep(seed, (uint32_t)v, x, colouring, slot, t)) col_out[k++] = x;
         }
         row_out[v + 1] = k;
     }

@@ -120,6 +120,12 @@ def lib():
             L.og_color.argtypes = [u64, u64, u32, u32, u32]
             L.og_sparsify.restype = u64
             L.og_sparsify.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.og_bes_threshold.restype = u64
+            L.og_bes_threshold.argtypes = [dbl]
+            L.og_bes_keep.restype = i32
+            L.og_bes_keep.argtypes = [u64, u32, u32, u32, u32, u64]
+            L.og_bes_sparsify.restype = u64
+            L.og_bes_sparsify.argtypes = [C.c_void_p, u64, u32, u32, u64, C.c_void_p, C.c_void_p]
             L.og_exact_count.restype = u64
             L.og_exact_count.argtypes = [C.c_void_p, P(Plan)]
             L.og_flog2p1.restype = C.c_float
@@ -272,6 +278,23 @@ def sparsify(g, cols):
     row = np.zeros(g.n + 1, dtype=np.uint64)
     col = np.zeros(max(g.nnz, 1), dtype=np.uint32)
     kept = lib().og_sparsify(g.h, cols.ctypes.data, row.ctypes.data, col.ctypes.data)
+    return row, col[:kept].copy()
+
+
+def bes_threshold(p):
+    """t with keep probability t / 2^32 (Algorithm 2's p)."""
+    return lib().og_bes_threshold(p)
+
+
+def bes_keep(seed, u, w, t, colouring=0, slot=0):
+    return bool(lib().og_bes_keep(seed, u, w, colouring, slot, t))
+
+
+def bes_sparsify(g, seed, t, colouring=0, slot=0):
+    """Bernoulli edge sparsification (Algorithm 2): the kept CSR."""
+    row = np.zeros(g.n + 1, dtype=np.uint64)
+    col = np.zeros(max(g.nnz, 1), dtype=np.uint32)
+    kept = lib().og_bes_sparsify(g.h, seed, colouring, slot, t, row.ctypes.data, col.ctypes.data)
     return row, col[:kept].copy()
 
 

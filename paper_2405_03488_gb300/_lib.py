@@ -41,7 +41,8 @@ class Config(C.Structure):
     _fields_ = [("window", C.c_uint64), ("n_min", C.c_uint64), ("n_max", C.c_uint64),
                 ("max_seconds", C.c_double), ("colors", C.c_uint32), ("slot", C.c_uint32),
                 ("verify", C.c_uint32), ("grid_blocks", C.c_uint32), ("block_warps", C.c_uint32),
-                ("cap", C.c_uint32), ("mlp", C.POINTER(MLP)), ("selector", C.POINTER(MLP))]
+                ("cap", C.c_uint32), ("mlp", C.POINTER(MLP)), ("selector", C.POINTER(MLP)),
+                ("edge_p", C.c_double), ("samplers", C.c_uint32), ("pad_", C.c_uint32)]
 
 
 class HybridInfo(C.Structure):
@@ -77,6 +78,16 @@ class Sums(C.Structure):
     _fields_ = [("n", C.c_uint64), ("hits", C.c_uint64), ("sum", C.c_double), ("sumsq", C.c_double)]
 
 
+class Partial(C.Structure):
+    _fields_ = [("sum", C.c_double), ("sumsq", C.c_double), ("hits", C.c_uint64), ("n", C.c_uint64)]
+
+
+class Window(C.Structure):
+    _fields_ = [("sum", C.c_double), ("sumsq", C.c_double), ("hits", C.c_uint64), ("n", C.c_uint64),
+                ("rounds", C.c_uint64), ("mu", C.c_double), ("half", C.c_double), ("eps_hat", C.c_double),
+                ("converged", C.c_uint32), ("active", C.c_uint32)]
+
+
 # (name, restype, argtypes): every exported entry point of include/gpm.h
 P = C.POINTER
 _V = C.c_void_p
@@ -92,6 +103,9 @@ SIGNATURES = [
     ("gpm_mlp_train", _i32, [_V, _V, _V, _u64, _u32, _u32, C.c_float, _V, _V, P(_dbl)]),
     ("gpm_sample_sums", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), P(Sums)]),
     ("gpm_sample_sums_static", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), P(Sums)]),
+    ("gpm_sample_partials", _i32, [_V, P(Pattern), _u64, _u64, _u64, _u32, _u32, P(Config), _V, P(_u64)]),
+    ("gpm_merge_partials", _i32, [_V, _u64, P(Sums)]),
+    ("gpm_window_update", _i32, [P(Window), P(Sums), _dbl, _dbl, _u64, _u64]),
     ("gpm_trace", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), _V]),
     ("gpm_exact_count", _i32, [_V, P(Pattern), P(_u64)]),
     ("gpm_mlp_scores", _i32, [_V, P(MLP), _V, _u64, _V]),
@@ -99,6 +113,7 @@ SIGNATURES = [
     ("gpm_proposal_features", _i32, [_V, P(Pattern), _V, _u64, _V, _V, P(_u64)]),
     ("gpm_train_proposal", _i32, [_V, P(Pattern), _u64, _u64, _u32, _u32, C.c_float, _V, _V, P(_dbl), P(_u64)]),
     ("gpm_sparsify", _i32, [_V, _u32, _u64, _u32, _u32, _V, _V, P(_u64)]),
+    ("gpm_sparsify_edges", _i32, [_V, _dbl, _u64, _u32, _u32, _V, _V, P(_u64)]),
     ("gpm_abort", _i32, [_V]),
     ("gpm_plan", _i32, [P(Pattern), P(_i32), P(_i32), P(_i32), P(_i32), P(_i32)]),
     ("gpm_normal_quantile", _dbl, [_dbl]),

@@ -15,6 +15,8 @@ RECORD_DTYPE = np.dtype([("factor", np.uint64, _lib.MAX_K), ("w_u64", np.uint64)
                          ("vert", np.uint32, _lib.MAX_K), ("aux", np.uint32, _lib.MAX_K), ("hit", np.uint8),
                          ("depth", np.uint8), ("overflow", np.uint8), ("pad", np.uint8, 5)])
 assert RECORD_DTYPE.itemsize == C.sizeof(_lib.SampleRecord)
+PARTIAL_DTYPE = np.dtype([("sum", np.float64), ("sumsq", np.float64), ("hits", np.uint64), ("n", np.uint64)])
+assert PARTIAL_DTYPE.itemsize == C.sizeof(_lib.Partial)
 
 
 def pattern(spec, induced=None):
@@ -148,6 +150,21 @@ class Graph:
               "gpm_sample_sums")
         return out
 
+    def sample_partials(self, pat, seed, first, count, rank=0, world=1, **cfg):
+        """Per-chunk partials of the 64-sample chunks c = rank (mod world) of
+        [first, first + count), in chunk order (a structured array with fields
+        sum, sumsq, hits, n)."""
+        nchunks = (count + 63) // 64
+        mine = max(0, (nchunks - rank + world - 1) // world) if nchunks > rank else 0
+        out = np.zeros(max(mine, 1), dtype=PARTIAL_DTYPE)
+        n = C.c_uint64()
+        pp = pattern(pat)
+        c = config(**cfg)
+        check(_lib.load().gpm_sample_partials(self.h, C.byref(pp), seed, first, count, rank, world, C.byref(c),
+                                              C.c_void_p(out.ctypes.data), C.byref(n)), "gpm_sample_partials")
+        assert n.value == mine
+        return out[:mine]
+
     def trace(self, pat, seed, first, count, **cfg):
         recs = np.zeros(count, dtype=RECORD_DTYPE)
         pp = pattern(pat)
@@ -169,6 +186,15 @@ class Graph:
         kept = C.c_uint64()
         check(_lib.load().gpm_sparsify(self.h, colors, seed, colouring, slot, C.c_void_p(row.data_ptr()),
                                        C.c_void_p(col.data_ptr()), C.byref(kept)), "gpm_sparsify")
+        return row, col[:kept.value]
+
+    def sparsify_edges(self, p, seed, colouring=0, slot=0):
+        """Bernoulli edge sparsification (keep probability p) into new CUDA tensors (row_ptr, col)."""
+        row = torch.empty(self.n + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(max(self.nnz, 1), dtype=torch.int32, device="cuda")
+        kept = C.c_uint64()
+        check(_lib.load().gpm_sparsify_edges(self.h, p, seed, colouring, slot, C.c_void_p(row.data_ptr()),
+                                             C.c_void_p(col.data_ptr()), C.byref(kept)), "gpm_sparsify_edges")
         return row, col[:kept.value]
 
     def abort(self):

@@ -158,20 +158,8 @@ __global__ void __launch_bounds__(1024) batch_reduce_check(const Partial *__rest
         J.hits += s_hits[0];
         J.n += s_n[0];
         J.rounds += 1;
-        const double nn = (double)J.n;
-        const double mu = J.sum / nn;
-        double var = J.sumsq / nn - mu * mu;
-        if (var < 0.0) var = 0.0;
-        const double sigma = sqrt(var / nn);
-        J.mu = mu;
-        J.half = ba.z * sigma;
-        J.eps_hat = (mu > 0.0) ? ba.z * sigma / mu : INFINITY;
-        if (J.n >= J.n_min && mu > 0.0 && J.eps_hat <= J.eps) {
-            J.converged = 1;
-            J.active = 0;
-        } else if (J.n >= J.n_max) {
-            J.active = 0;
-        }
+        window_test(J.sum, J.sumsq, J.n, ba.z, J.eps, J.n_min, J.n_max, &J.mu, &J.half, &J.eps_hat, &J.converged,
+                    &J.active);
     }
 }
 

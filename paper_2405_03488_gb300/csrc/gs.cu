@@ -9,6 +9,16 @@
 // of Philox4x32-10 at counter (v_lo, v_hi, colouring, slot << 8 | 2), key =
 // seed, a stream disjoint from the sampling words.
 //
+// Bernoulli edge sparsification (Algorithm 2) keeps every edge independently
+// with probability p = t / 2^32: edge {u, w} stays iff the first word of
+// Philox4x32-10 at counter (min(u, w), max(u, w), colouring, slot << 8 | 3) is
+// below t, one decision for both CSR entries; a match with l edges survives
+// with probability p^l, so C' (2^32 / t)^l estimates C for edge-induced
+// counting (removing edges can create vertex-induced occurrences, so that
+// case is refused).  Several independent sparsifications ("samplers") are
+// averaged; with R >= 2 their sample standard deviation s gives the interval
+// half width z s / sqrt(R).
+//
 // Sparsification reads every edge once and writes the kept ones (the paper's
 // preprocessing cost |E| (w1 + p w2), Sec. 4.4): a colour pass, a count pass
 // and a compaction pass (one warp per vertex, ballot compaction keeps the
@@ -56,6 +66,48 @@ __global__ void keep_count(const uint64_t *__restrict__ row_ptr, const uint32_t 
 #pragma unroll
         for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
         if (lane == 0) cnt[v] = c;
+    }
+}
+
+__device__ __forceinline__ bool bes_keep(uint64_t seed, uint32_t u, uint32_t w, uint32_t colouring, uint32_t slot,
+                                         uint64_t t) {
+    const uint32_t lo = u < w ? u : w, hi = u < w ? w : u;
+    const Philox4 o = philox10(lo, hi, colouring, (slot << 8) | 3u, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return (uint64_t)o.x < t;
+}
+
+__global__ void bes_count(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ col, uint64_t n,
+                          uint64_t seed, uint32_t colouring, uint32_t slot, uint64_t t, uint64_t *cnt) {
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const unsigned lane = threadIdx.x & 31u;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = warp; v < n; v += nw) {
+        const uint64_t b = row_ptr[v], e = row_ptr[v + 1];
+        uint64_t c = 0;
+        for (uint64_t i = b + lane; i < e; i += 32) c += bes_keep(seed, (uint32_t)v, __ldg(col + i), colouring, slot, t);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+        if (lane == 0) cnt[v] = c;
+    }
+}
+
+__global__ void bes_write(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ col, uint64_t n,
+                          uint64_t seed, uint32_t colouring, uint32_t slot, uint64_t t,
+                          const uint64_t *__restrict__ row_out, uint32_t *col_out) {
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const unsigned lane = threadIdx.x & 31u;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t v = warp; v < n; v += nw) {
+        const uint64_t b = row_ptr[v], e = row_ptr[v + 1];
+        uint64_t pos = row_out[v];
+        for (uint64_t base = b; base < e; base += 32) {
+            const uint64_t i = base + lane;
+            const uint32_t x = i < e ? __ldg(col + i) : 0u;
+            const bool keep = i < e && bes_keep(seed, (uint32_t)v, x, colouring, slot, t);
+            const unsigned m = __ballot_sync(kFull, keep);
+            if (keep) col_out[pos + __popc(m & ((1u << lane) - 1u))] = x;
+            pos += __popc(m);
+        }
     }
 }
 
@@ -320,7 +372,7 @@ gpm_status exact_count_plan(gpm_graph *h, const Plan &p, uint64_t *out, float *k
 // Colour + sparsify into freshly allocated device arrays (caller frees).
 gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colouring, uint32_t slot,
                           uint64_t **row_out, uint32_t **col_out, uint64_t *kept, uint64_t *user_row,
-                          uint32_t *user_col) {
+                          uint32_t *user_col, uint64_t bes_t) {
     const uint64_t n = h->d.n;
     cudaStream_t st = h->stream;
     uint32_t *colours = nullptr;
@@ -338,7 +390,9 @@ gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colo
     const unsigned blocks_v = (unsigned)((n + 255) / 256);
     const uint64_t warps = n < (1ull << 22) ? (n ? n : 1) : (1ull << 22);
     const unsigned blocks_w = (unsigned)((warps * 32 + 255) / 256);
-    if (n) {
+    if (n && bes_t) {
+        bes_count<<<blocks_w, 256, 0, st>>>(h->d.row_ptr, h->d.col, n, seed, colouring, slot, bes_t, cnt);
+    } else if (n) {
         colour_kernel<<<blocks_v, 256, 0, st>>>(n, c, seed, colouring, slot, colours);
         keep_count<<<blocks_w, 256, 0, st>>>(h->d.row_ptr, h->d.col, colours, n, cnt);
     }
@@ -349,7 +403,10 @@ gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colo
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && !col) e = cudaMallocAsync((void **)&col, sizeof(uint32_t) * (k ? k : 1), st);
     if (e == cudaSuccess && n) {
-        keep_write<<<blocks_w, 256, 0, st>>>(h->d.row_ptr, h->d.col, colours, n, row, col);
+        if (bes_t)
+            bes_write<<<blocks_w, 256, 0, st>>>(h->d.row_ptr, h->d.col, n, seed, colouring, slot, bes_t, row, col);
+        else
+            keep_write<<<blocks_w, 256, 0, st>>>(h->d.row_ptr, h->d.col, colours, n, row, col);
         e = cudaGetLastError();
     }
     cudaFreeAsync(colours, st);
@@ -365,44 +422,91 @@ gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colo
     return GPM_OK;
 }
 
-gpm_status gs_estimate(gpm_graph *h, const Plan &p, uint64_t seed, const gpm_config *cfg, gpm_result *out) {
+static uint64_t bes_threshold(double p) { return p >= 1.0 ? (1ull << 32) : (uint64_t)std::floor(p * 4294967296.0); }
+
+gpm_status gs_estimate(gpm_graph *h, const Plan &p, uint64_t seed, double delta, const gpm_config *cfg,
+                       gpm_result *out) {
     const auto t0 = std::chrono::steady_clock::now();
     const uint32_t c = (cfg && cfg->colors) ? cfg->colors : 8;
     const uint32_t slot = cfg ? cfg->slot : 0;
-    uint64_t *row = nullptr;
-    uint32_t *col = nullptr;
-    uint64_t kept = 0;
-    gpm_status st = sparsify_alloc(h, c, seed, 0, slot, &row, &col, &kept, nullptr, nullptr);
-    if (st != GPM_OK) return st;
-    gpm_graph *gs = nullptr;
-    st = gpm_load_csr(h->d.n, row, col, GPM_DEVICE_PTRS, h->stream, &gs);
-    const auto t1 = std::chrono::steady_clock::now();
-    uint64_t cp = 0;
-    float ms = 0.f;
+    const uint32_t R = (cfg && cfg->samplers) ? cfg->samplers : 1;
+    const double ep = cfg ? cfg->edge_p : 0.0;
+    if (!(ep >= 0.0 && ep <= 1.0)) {
+        set_error("GS: edge_p must be in [0, 1]");
+        return GPM_ERR_ARG;
+    }
+    const uint64_t t = ep > 0.0 ? bes_threshold(ep) : 0;
+    if (ep > 0.0 && t == 0) {
+        set_error("GS: edge_p below 2^-32");
+        return GPM_ERR_ARG;
+    }
+    if (ep > 0.0 && p.induced) {
+        set_error("GS: Bernoulli edge sparsification has no unbiased vertex-induced estimator");
+        return GPM_ERR_UNSUPPORTED;
+    }
+    // scale of one sparsified count: c^(k-1) (colours) or (2^32 / t)^l (edges),
+    // l = the pattern's edge count, as l multiplications left to right
+    double scale = 1.0;
+    if (ep > 0.0) {
+        int l = 0;
+        for (int j = 0; j < p.k; j++) l += __builtin_popcount(p.back[j]);
+        for (int q = 0; q < l; q++) scale *= 4294967296.0 / (double)t;
+    } else {
+        scale = std::pow((double)c, (double)(p.k - 1));
+    }
     const double budget = cfg ? cfg->max_seconds : 0.0;
     gpm_status late = GPM_OK;
-    if (st == GPM_OK) {
-        st = exact_count_plan(gs, p, &cp, &ms, budget);
-        if (st == GPM_ERR_NOT_CONVERGED) {
-            late = st;
-            st = GPM_OK;
+    double t_pre = 0.0, t_search = 0.0, mean = 0.0;
+    uint64_t total = 0;
+    std::vector<double> est(R);
+    for (uint32_t r = 0; r < R; r++) {
+        const auto ta = std::chrono::steady_clock::now();
+        uint64_t *row = nullptr;
+        uint32_t *col = nullptr;
+        uint64_t kept = 0;
+        gpm_status st = sparsify_alloc(h, c, seed, r, slot, &row, &col, &kept, nullptr, nullptr, t);
+        if (st != GPM_OK) return st;
+        gpm_graph *gs = nullptr;
+        st = gpm_load_csr(h->d.n, row, col, GPM_DEVICE_PTRS, h->stream, &gs);
+        t_pre += std::chrono::duration<double>(std::chrono::steady_clock::now() - ta).count();
+        uint64_t cp = 0;
+        float ms = 0.f;
+        if (st == GPM_OK) {
+            st = exact_count_plan(gs, p, &cp, &ms, budget);
+            if (st == GPM_ERR_NOT_CONVERGED) {
+                late = st;
+                st = GPM_OK;
+            }
         }
+        if (gs) gpm_free_graph(gs);
+        cudaFree(row);
+        cudaFree(col);
+        if (st != GPM_OK) return st;
+        t_search += ms * 1e-3;
+        total += cp;
+        est[r] = (double)cp * scale;
+        mean += est[r];
     }
-    if (gs) gpm_free_graph(gs);
-    cudaFree(row);
-    cudaFree(col);
-    if (st != GPM_OK) return st;
-    out->exact_count = cp;
-    out->estimate = (double)cp * std::pow((double)c, (double)(p.k - 1));
+    mean /= (double)R;
+    out->exact_count = total;
+    out->estimate = mean;
     out->ci_half_width = NAN;
     out->eps_hat = NAN;
+    if (R >= 2) {
+        double ss = 0.0;
+        for (uint32_t r = 0; r < R; r++) ss += (est[r] - mean) * (est[r] - mean);
+        const double s = std::sqrt(ss / (double)(R - 1));
+        out->ci_half_width = normal_quantile(1.0 - delta / 2.0) * (s / std::sqrt((double)R));
+        out->eps_hat = mean > 0.0 ? out->ci_half_width / mean : INFINITY;
+    }
+    out->samples = R;
     out->scheme_used = GPM_GS;
     out->converged = late == GPM_OK ? 1 : 0;
-    out->t_preproc_s = std::chrono::duration<double>(t1 - t0).count();
-    out->t_sample_s = ms * 1e-3;
-    out->kernel_launches += 7;
+    out->t_preproc_s = t_pre;
+    out->t_sample_s = t_search;
+    out->kernel_launches += 7 * (uint64_t)R;
     out->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (late != GPM_OK) set_error("GS: exact count on the sparsified graph hit max_seconds");
+    if (late != GPM_OK) set_error("GS: exact count on a sparsified graph hit max_seconds");
     return late;
 }
 
@@ -420,6 +524,15 @@ extern "C" gpm_status gpm_exact_count(gpm_graph *h, const gpm_pattern *pattern, 
         return GPM_ERR_ARG;
     }
     return exact_count_plan(h, p, out, nullptr, 0.0);
+}
+
+extern "C" gpm_status gpm_sparsify_edges(gpm_graph *h, double p, uint64_t seed, uint32_t colouring, uint32_t slot,
+                                         uint64_t *row_out, uint32_t *col_out, uint64_t *kept) {
+    if (!h || !row_out || !col_out || !kept || !(p > 0.0) || bes_threshold(p) == 0) {
+        set_error("gpm_sparsify_edges: null argument or p not in (2^-32, 1]");
+        return GPM_ERR_ARG;
+    }
+    return sparsify_alloc(h, 1, seed, colouring, slot, nullptr, nullptr, kept, row_out, col_out, bes_threshold(p));
 }
 
 extern "C" gpm_status gpm_sparsify(gpm_graph *h, uint32_t colors, uint64_t seed, uint32_t colouring, uint32_t slot,

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include <string>
 #include <vector>
 
@@ -53,15 +55,76 @@ struct Totals {
 
 void set_error(const std::string &msg);
 
+// Single correctly rounded FP64 operations on host and device (the device
+// would otherwise be free to fuse a multiply and an add).
+__host__ __device__ inline double rn_add(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return __dadd_rn(a, b);
+#else
+    return a + b;
+#endif
+}
+__host__ __device__ inline double rn_sub(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return __dsub_rn(a, b);
+#else
+    return a - b;
+#endif
+}
+__host__ __device__ inline double rn_mul(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+__host__ __device__ inline double rn_div(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return __ddiv_rn(a, b);
+#else
+    return a / b;
+#endif
+}
+__host__ __device__ inline double rn_sqrt(double a) {
+#ifdef __CUDA_ARCH__
+    return __dsqrt_rn(a);
+#else
+    return std::sqrt(a);
+#endif
+}
+
+// Algorithm 3's window test on the running totals (Eq. equ:error), shared by
+// the device (batch_reduce_check) and the host (gpm_window_update).
+__host__ __device__ inline void window_test(double sum, double sumsq, uint64_t n, double z, double eps,
+                                            uint64_t n_min, uint64_t n_max, double *mu_out, double *half_out,
+                                            double *eps_hat_out, uint32_t *converged, uint32_t *active) {
+    const double nn = (double)n;
+    const double mu = rn_div(sum, nn);
+    double var = rn_sub(rn_div(sumsq, nn), rn_mul(mu, mu));
+    if (var < 0.0) var = 0.0;
+    const double sigma = rn_sqrt(rn_div(var, nn));
+    const double half = rn_mul(z, sigma);
+    *mu_out = mu;
+    *half_out = half;
+    *eps_hat_out = (mu > 0.0) ? rn_div(half, mu) : INFINITY;
+    if (n >= n_min && mu > 0.0 && *eps_hat_out <= eps) {
+        *converged = 1;
+        *active = 0;
+    } else if (n >= n_max) {
+        *active = 0;
+    }
+}
+
 }  // namespace gpm
 
 struct gpm_graph;
 namespace gpm {
 gpm_status exact_count_plan(gpm_graph *h, const Plan &p, uint64_t *out, float *kernel_ms, double max_seconds);
-gpm_status gs_estimate(gpm_graph *h, const Plan &p, uint64_t seed, const gpm_config *cfg, gpm_result *out);
+gpm_status gs_estimate(gpm_graph *h, const Plan &p, uint64_t seed, double delta, const gpm_config *cfg,
+                       gpm_result *out);
 gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colouring, uint32_t slot,
                           uint64_t **row_out, uint32_t **col_out, uint64_t *kept, uint64_t *user_row,
-                          uint32_t *user_col);
+                          uint32_t *user_col, uint64_t bes_t = 0);
 double normal_quantile(double p);
 gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const double *eps, double delta,
                           uint64_t seed, const gpm_config *cfg, gpm_result *results, int mode);

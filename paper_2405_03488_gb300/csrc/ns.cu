@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOC
         if (lane == 0) c = atomicAdd(a.counter, 1u);
         c = __shfl_sync(kFull, c, 0);
         if (c >= a.nchunks) break;
-        const uint64_t s0 = a.first + (uint64_t)c * a.chunk;
+        const uint64_t s0 = a.first + (uint64_t)c * a.stride * a.chunk;
         const uint64_t s1 = (s0 + a.chunk < end) ? s0 + a.chunk : end;
         double sum = 0.0, sumsq = 0.0;
         uint64_t hits = 0;
@@ -185,13 +185,19 @@ static gpm_status ensure_partials(gpm_graph *h, uint64_t n) {
 
 // One sampling launch over [first, first + count) plus the chunk-order
 // reduction into h->totals[0] (accumulate = fold into the running totals).
+// With world > 1 only the chunks c = rank (mod world) of the range are drawn
+// (h->partials then holds them in that order).
 static gpm_status run_block(gpm_graph *h, const Plan &p, int mode, uint64_t seed, uint32_t slot, uint64_t first,
                             uint64_t count, const gpm_config *cfg, int accumulate, gpm_sample_record *trace,
-                            float *kernel_ms) {
+                            float *kernel_ms, uint32_t rank = 0, uint32_t world = 1, uint64_t *nchunks_out = nullptr) {
     Shape sh = pick_shape(h, cfg, count);
     if (sh.cap == 0) sh.cap = fit_cap(h, 0, sh.warps, mode);   // ns_kernel has no static shared memory
     if (mode == MODE_LEARNED && sh.cap < kLearnedMax) sh.cap = kLearnedMax;
-    const uint64_t nchunks = (count + sh.chunk - 1) / sh.chunk;
+    const uint64_t all_chunks = (count + sh.chunk - 1) / sh.chunk;
+    const uint64_t nchunks = (rank < all_chunks) ? (all_chunks - rank + world - 1) / world : 0;
+    if (nchunks_out) *nchunks_out = nchunks;
+    first += (uint64_t)rank * sh.chunk;
+    count = (nchunks > 0) ? count - (uint64_t)rank * sh.chunk : 0;
     if (nchunks >= (1ull << 31)) {
         set_error("too many samples in one launch");
         return GPM_ERR_ARG;
@@ -209,6 +215,7 @@ static gpm_status run_block(gpm_graph *h, const Plan &p, int mode, uint64_t seed
     a.cap = sh.cap;
     a.chunk = sh.chunk;
     a.nchunks = (uint32_t)nchunks;
+    a.stride = world;
     std::memset(&a.mlp, 0, sizeof(a.mlp));
     if (mode == MODE_LEARNED) a.mlp = *cfg->mlp;
     if (cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), h->stream) != cudaSuccess) {
@@ -353,6 +360,100 @@ extern "C" gpm_status gpm_sample_sums(gpm_graph *h, const gpm_pattern *pattern, 
     out->hits = h->totals_host->hits;
     out->sum = h->totals_host->sum;
     out->sumsq = h->totals_host->sumsq;
+    return GPM_OK;
+}
+
+extern "C" gpm_status gpm_sample_partials(gpm_graph *h, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
+                                          uint64_t count, uint32_t rank, uint32_t world, const gpm_config *cfg,
+                                          gpm_partial *out, uint64_t *n_out) {
+    if (!h || !n_out || world == 0 || rank >= world) {
+        set_error("gpm_sample_partials: null argument or rank >= world");
+        return GPM_ERR_ARG;
+    }
+    Plan p;
+    gpm_status st = plan_or_error(pattern, &p);
+    if (st != GPM_OK) return st;
+    *n_out = 0;
+    const uint64_t mine = (count + kChunk - 1) / kChunk > rank ? ((count + kChunk - 1) / kChunk - rank + world - 1) / world : 0;
+    if (mine == 0) return GPM_OK;
+    if (!out) {
+        set_error("gpm_sample_partials: null output array");
+        return GPM_ERR_ARG;
+    }
+    uint64_t n = 0;
+    st = run_block(h, p, mode_of(cfg), seed, cfg ? cfg->slot : 0, first, count, cfg, 0, nullptr, nullptr, rank, world,
+                   &n);
+    if (st != GPM_OK) return st;
+    static_assert(sizeof(gpm_partial) == sizeof(Partial), "partial layout");
+    if (cudaMemcpy(out, h->partials, sizeof(Partial) * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("gpm_sample_partials: copy back failed");
+        return GPM_ERR_CUDA;
+    }
+    *n_out = n;
+    return GPM_OK;
+}
+
+extern "C" gpm_status gpm_merge_partials(const gpm_partial *parts, uint64_t n, gpm_sums *out) {
+    if (!out || (n && !parts) || n >= (1ull << 32)) {
+        set_error("gpm_merge_partials: null argument or n >= 2^32");
+        return GPM_ERR_ARG;
+    }
+    // the reduction of reduce_partials / batch_reduce_check, written out on the host
+    std::vector<double> s_sum(1024), s_sq(1024);
+    std::vector<uint64_t> s_hits(1024), s_n(1024);
+    const uint32_t per = (uint32_t)((n + 1023) / 1024);
+    for (uint32_t t = 0; t < 1024; t++) {
+        const uint64_t b = (uint64_t)t * per;
+        const uint64_t e = (b + per < n) ? b + per : n;
+        double sum = 0.0, sq = 0.0;
+        uint64_t hits = 0, cnt = 0;
+        for (uint64_t i = b; i < e; i++) {
+            sum = rn_add(sum, parts[i].sum);
+            sq = rn_add(sq, parts[i].sumsq);
+            hits += parts[i].hits;
+            cnt += parts[i].n;
+        }
+        s_sum[t] = sum;
+        s_sq[t] = sq;
+        s_hits[t] = hits;
+        s_n[t] = cnt;
+    }
+    for (uint32_t hh = 512; hh; hh >>= 1)
+        for (uint32_t t = 0; t < hh; t++) {
+            s_sum[t] = rn_add(s_sum[t], s_sum[t + hh]);
+            s_sq[t] = rn_add(s_sq[t], s_sq[t + hh]);
+            s_hits[t] += s_hits[t + hh];
+            s_n[t] += s_n[t + hh];
+        }
+    out->n = s_n[0];
+    out->hits = s_hits[0];
+    out->sum = s_sum[0];
+    out->sumsq = s_sq[0];
+    return GPM_OK;
+}
+
+extern "C" gpm_status gpm_window_update(gpm_window *w, const gpm_sums *win, double z, double eps, uint64_t n_min,
+                                       uint64_t n_max) {
+    if (!w || !win || !(eps > 0.0) || !(z > 0.0)) {
+        set_error("gpm_window_update: null argument, eps <= 0 or z <= 0");
+        return GPM_ERR_ARG;
+    }
+    if (!w->active) {
+        set_error("gpm_window_update: the run has stopped");
+        return GPM_ERR_ARG;
+    }
+    // as batch_reduce_check: the first window is assigned, later ones added
+    if (w->rounds == 0) {
+        w->sum = win->sum;
+        w->sumsq = win->sumsq;
+    } else {
+        w->sum = rn_add(w->sum, win->sum);
+        w->sumsq = rn_add(w->sumsq, win->sumsq);
+    }
+    w->hits += win->hits;
+    w->n += win->n;
+    w->rounds += 1;
+    window_test(w->sum, w->sumsq, w->n, z, eps, n_min, n_max, &w->mu, &w->half, &w->eps_hat, &w->converged, &w->active);
     return GPM_OK;
 }
 
@@ -556,7 +657,7 @@ static gpm_status hybrid_estimate(gpm_graph *h, const Plan &p, double eps, doubl
     gpm_status st = hybrid_decide(h, p, eps, delta, seed, cfg, &hm, nullptr);
     if (st != GPM_OK) return st;
     const double t_pilot = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (hm.choose_gs) st = gs_estimate(h, p, seed, cfg, out);
+    if (hm.choose_gs) st = gs_estimate(h, p, seed, delta, cfg, out);
     else st = ns_estimate(h, p, eps, delta, seed, cfg, out);
     out->t_pilot_s = t_pilot;
     out->kernel_launches += 6;
@@ -598,7 +699,11 @@ extern "C" gpm_status gpm_estimate(gpm_graph *h, const gpm_pattern *pattern, gpm
         case GPM_NS:
             return ns_estimate(h, p, eps, delta, seed, cfg, out);
         case GPM_GS:
-            return gs_estimate(h, p, seed, cfg, out);
+            if (!(delta > 0.0 && delta < 1.0)) {
+                set_error("delta must be in (0, 1)");
+                return GPM_ERR_ARG;
+            }
+            return gs_estimate(h, p, seed, delta, cfg, out);
         case GPM_NS_LEARNED:
             return learned_estimate(h, p, eps, delta, seed, cfg, out);
         case GPM_HYBRID:
@@ -714,6 +819,7 @@ extern "C" gpm_status gpm_sample_sums_static(gpm_graph *h, const gpm_pattern *pa
     a.cap = sh.cap;
     a.chunk = sh.chunk;
     a.nchunks = (uint32_t)nchunks;
+    a.stride = 1;
     std::memset(&a.mlp, 0, sizeof(a.mlp));
     if (mode == MODE_LEARNED) a.mlp = *cfg->mlp;
     cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(unsigned int), h->stream);

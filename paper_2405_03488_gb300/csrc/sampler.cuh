@@ -45,6 +45,7 @@ struct RunArgs {
     uint32_t cap;                 // entries per on-chip candidate buffer
     uint32_t chunk;               // samples per chunk
     uint32_t nchunks;
+    uint32_t stride;              // chunks of the range between consecutive chunks of this launch
     gpm_mlp mlp;                  // learned proposal weights (device, BF16)
 };
 

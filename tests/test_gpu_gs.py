@@ -1,11 +1,13 @@
 """GPU parity of colour sparsification, exact counting, the GS estimate and
 the hybrid choice against the CPU oracle (integers bit-exact)."""
+import math
+
 import numpy as np
 import pytest
 import torch
 
 from oracle import oracle as O
-from paper_2405_03488_gb300 import api
+from paper_2405_03488_gb300 import _lib, api
 from paper_2405_03488_gb300 import graphs as G
 
 pytestmark = pytest.mark.gpu
@@ -133,3 +135,70 @@ def test_selector_head_decides_the_hybrid():
             assert r["estimate"] == g.estimate(name, scheme=api.GS, seed=3)["estimate"]
         else:
             assert r["converged"] == 1
+
+
+@pytest.mark.parametrize("prob,colouring,slot", [(0.5, 0, 0), (0.3, 2, 1), (1.0, 0, 3), (0.05, 7, 0)])
+def test_edge_sparsify_bit_exact(prob, colouring, slot):
+    rp, col = G.erdos_renyi(5000, 0.004, seed=6)
+    g, og = pair(rp, col)
+    row_d, col_d = g.sparsify_edges(prob, seed=99, colouring=colouring, slot=slot)
+    row_o, col_o = O.bes_sparsify(og, 99, O.bes_threshold(prob), colouring, slot)
+    assert np.array_equal(row_d.cpu().numpy().astype(np.uint64), row_o)
+    assert np.array_equal(col_d.cpu().numpy().astype(np.uint32), col_o)
+
+
+def scaled_counts(og, name, seed, R, prob=None, c=None):
+    """Per-sampler scaled counts from the oracle: sparsification r, exact count, scale."""
+    k, edges = G.pattern(name)
+    p = O.plan(k, edges)
+    out = []
+    for r in range(R):
+        if prob is not None:
+            t = O.bes_threshold(prob)
+            row, cc = O.bes_sparsify(og, seed, t, colouring=r)
+            scale = 1.0
+            for _ in range(len(edges)):
+                scale *= 4294967296.0 / t
+        else:
+            row, cc = O.sparsify(og, O.colors(og.n, c, seed, colouring=r))
+            scale = float(c) ** (k - 1)
+        out.append((O.exact_count(O.Graph(row, cc), p), scale))
+    return out
+
+
+@pytest.mark.parametrize("name,prob,c,R", [("triangle", 0.5, None, 1), ("4-cycle", 0.6, None, 5),
+                                           ("house", 0.7, None, 3), ("4-clique", None, 4, 6)])
+def test_gs_samplers_and_edge_mode_match_oracle(name, prob, c, R):
+    rp, col = G.erdos_renyi(2000, 0.03, seed=7)
+    g, og = pair(rp, col)
+    kw = {"samplers": R}
+    if prob is not None:
+        kw["edge_p"] = prob
+    else:
+        kw["colors"] = c
+    r = g.estimate(name, scheme=api.GS, seed=11, delta=0.05, **kw)
+    parts = scaled_counts(og, name, 11, R, prob, c)
+    ests = [cnt * s for cnt, s in parts]
+    mean = 0.0
+    for e in ests:
+        mean += e
+    mean /= R
+    assert r["exact_count"] == sum(cnt for cnt, _ in parts)
+    assert r["estimate"] == mean and r["samples"] == R
+    if R == 1:
+        assert np.isnan(r["ci_half_width"])
+    else:
+        ss = 0.0
+        for e in ests:
+            ss += (e - mean) * (e - mean)
+        half = api.normal_quantile(1 - 0.05 / 2) * (math.sqrt(ss / (R - 1)) / math.sqrt(R))
+        assert mean > 0
+        assert r["ci_half_width"] == half and r["eps_hat"] == half / mean
+
+
+def test_gs_edge_mode_refuses_vertex_induced_patterns():
+    rp, col = G.erdos_renyi(300, 0.05, seed=2)
+    g = api.Graph(rp.cuda(), col.cuda())
+    k, edges = G.pattern("4-cycle")
+    with pytest.raises(_lib.GpmError):
+        g.estimate((k, edges, True), scheme=api.GS, edge_p=0.5)

@@ -415,6 +415,67 @@ def test_sparsify_keeps_monochromatic_edges():
     assert O.validate(row, cc) == 0
 
 
+def test_bes_expectation_over_all_edge_subsets_is_exact():
+    """Bernoulli edge sparsification with p = 1/2: every subset of the m edges is
+    equally likely, and a match survives iff its l edges all stay, so the mean
+    of C' over all 2^m subsets is C 2^-l exactly (Algorithm 2: scale by p^-l,
+    l the pattern's edge count, not k - 1)."""
+    import itertools
+    rp, col = G.random_small(7, 0.55, 4)
+    rp, col = G.to_numpy(rp, col)
+    edges = [(u, int(x)) for u in range(len(rp) - 1) for x in col[rp[u]:rp[u + 1]] if u < x]
+    m = len(edges)
+    assert 8 <= m <= 14
+    g = O.Graph(rp, col)
+    for name in ("triangle", "4-cycle", "4-path", "diamond"):
+        k, pe = G.pattern(name)
+        p = O.plan(k, pe)
+        C = O.exact_count(g, p)
+        tot = 0
+        for keep in itertools.product((0, 1), repeat=m):
+            adj = [[] for _ in range(len(rp) - 1)]
+            for (u, w), kk in zip(edges, keep):
+                if kk:
+                    adj[u].append(w)
+                    adj[w].append(u)
+            row = np.zeros(len(rp), dtype=np.uint64)
+            cc = []
+            for u, a in enumerate(adj):
+                cc += sorted(a)
+                row[u + 1] = len(cc)
+            tot += O.exact_count(O.Graph(row, np.array(cc, dtype=np.uint32)), p)
+        assert Fraction(tot, 2 ** m) == Fraction(C, 2 ** len(pe)), name
+
+
+def test_bes_keep_is_word0_of_purpose3_block_on_the_unordered_pair():
+    seed = 123
+    assert O.bes_threshold(0.3) == 1288490188 and O.bes_threshold(1.0) == 1 << 32
+    assert O.bes_threshold(0.5) == 1 << 31
+    t = O.bes_threshold(0.3)
+    for (u, w) in ((0, 1), (7, 3), (100, 5), (2 ** 32 - 2, 17)):
+        lo, hi = min(u, w), max(u, w)
+        w0 = O.philox((lo, hi, 2, (5 << 8) | 3), (seed, 0))[0]
+        assert O.bes_keep(seed, u, w, t, colouring=2, slot=5) == (w0 < t)
+        assert O.bes_keep(seed, u, w, t, colouring=2, slot=5) == O.bes_keep(seed, w, u, t, colouring=2, slot=5)
+    rng = np.random.default_rng(1)
+    pairs = rng.integers(0, 1 << 20, size=(60000, 2))
+    frac = np.mean([O.bes_keep(seed, int(a), int(b), t) for a, b in pairs])
+    assert abs(frac - t / 2 ** 32) < 0.008            # 4 binomial standard deviations
+    assert all(O.bes_keep(seed, int(a), int(b), 1 << 32) for a, b in pairs[:200])
+
+
+def test_bes_sparsify_keeps_each_edge_once_for_both_directions():
+    rp, col = G.random_small(30, 0.4, 5)
+    g = og(rp, col)
+    t = O.bes_threshold(0.45)
+    row, cc = O.bes_sparsify(g, 9, t, colouring=1, slot=2)
+    assert O.validate(row, cc) == 0                    # symmetric, sorted, no loops
+    want = [(u, int(x)) for u in range(g.n) for x in col[rp[u]:rp[u + 1]].numpy()
+            if O.bes_keep(9, u, int(x), t, colouring=1, slot=2)]
+    got = [(u, int(x)) for u in range(g.n) for x in cc[row[u]:row[u + 1]]]
+    assert got == want
+
+
 # ------------------------------------------------------------------ validation
 def test_validate_detects_each_violation():
     rp, col = G.to_numpy(*G.complete(4))
