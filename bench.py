@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--config", default="rmat22",
-                    choices=["rmat22", "er-triangle", "rmat24-batch", "chunglu-needle", "rmat27", "selector"],
+                    choices=["rmat22", "er-triangle", "rmat24-batch", "chunglu-needle", "rmat27", "selector",
+                             "complex", "gs-variants"],
                     help="workload; the default is the headline R-MAT 22 run, the others print one "
                          "JSON line each for the companion workloads")
     ap.add_argument("--ncu-case", default=None, choices=["4-clique", "5-clique"],
@@ -386,6 +387,37 @@ def companion(args):
             out[name] = row
     elif args.config == "selector":
         out.update(selector_study(api, G))
+    elif args.config == "complex":
+        # the paper's non-clique patterns (edge-induced), NS to +-1% at 99% on R-MAT 22
+        rp, col = make_graph("cuda")
+        torch.cuda.synchronize()
+        g = api.Graph(rp, col)
+        out.update({"n": g.n, "m": g.m, "eps": EPS, "delta": DELTA})
+        for name in ("5-path", "house", "dumbbell"):
+            k, edges = G.pattern(name)
+            pat = (k, edges, False)
+            for w in range(args.warmup):
+                g.estimate(pat, eps=EPS, delta=DELTA, seed=100 + w, window=WINDOW, n_max=1 << 36, max_seconds=60.0)
+            r, t = _timed(lambda: g.estimate(pat, eps=EPS, delta=DELTA, seed=1, window=WINDOW, n_max=1 << 36,
+                                             max_seconds=60.0))
+            out[name] = {"seconds": t, "estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"],
+                         "hit_rate": r["hits"] / max(r["samples"], 1),
+                         "samples_per_s": r["samples"] / max(r["t_sample_s"], 1e-12), "converged": r["converged"]}
+    elif args.config == "gs-variants":
+        # colour (c = 8) against Bernoulli edge (p = 1/8) sparsification, 8 samplers each, on R-MAT 16;
+        # exact counts for reference
+        rp, col = G.rmat(16, 16, seed=4, device="cuda")
+        torch.cuda.synchronize()
+        g = api.Graph(rp, col)
+        out.update({"n": g.n, "m": g.m, "samplers": 8})
+        for name in ("triangle", "4-cycle"):
+            exact, te = _timed(lambda: g.exact_count(name))
+            row = {"exact": exact, "exact_s": te}
+            for label, kw in (("colour_c8", {"colors": 8}), ("edge_p0.125", {"edge_p": 0.125})):
+                r, t = _timed(lambda: g.estimate(name, scheme=api.GS, seed=5, delta=DELTA, samplers=8, **kw))
+                row[label] = {"seconds": t, "estimate": r["estimate"], "ci_half_width_99": r["ci_half_width"],
+                              "rel_err": abs(r["estimate"] - exact) / exact, "kept_matches": r["exact_count"]}
+            out[name] = row
     print(json.dumps(out))
 
 
