@@ -270,21 +270,24 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
     auto cleanup = [&]() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        // stream-ordered frees after the batch's own work
+        cudaStream_t fs = cs ? cs : h->stream;
+        pool_free(d_plans, fs);
+        pool_free(d_jobs, fs);
+        pool_free(d_ctl, fs);
+        pool_free(d_parts, fs);
         if (cs) cudaStreamDestroy(cs);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_a) cudaEventDestroy(ev_a);
         if (ev_b) cudaEventDestroy(ev_b);
         for (int i = 0; i < 2 * R; i++)
             if (ev_k[i]) cudaEventDestroy(ev_k[i]);
-        cudaFree(d_plans);
-        cudaFree(d_jobs);
-        cudaFree(d_ctl);
-        cudaFree(d_parts);
     };
-    if (cudaMalloc((void **)&d_plans, sizeof(Plan) * nj) != cudaSuccess ||
-        cudaMalloc((void **)&d_jobs, sizeof(BatchJob) * nj) != cudaSuccess ||
-        cudaMalloc((void **)&d_ctl, sizeof(BatchCtl)) != cudaSuccess ||
-        cudaMalloc((void **)&d_parts, sizeof(Partial) * cpj * nj) != cudaSuccess) {
+    // allocated on the handle's stream, which the batch stream waits for below
+    if (pool_alloc((void **)&d_plans, sizeof(Plan) * nj, h->stream) != cudaSuccess ||
+        pool_alloc((void **)&d_jobs, sizeof(BatchJob) * nj, h->stream) != cudaSuccess ||
+        pool_alloc((void **)&d_ctl, sizeof(BatchCtl), h->stream) != cudaSuccess ||
+        pool_alloc((void **)&d_parts, sizeof(Partial) * cpj * nj, h->stream) != cudaSuccess) {
         cleanup();
         set_error("batch: device allocation failed");
         return GPM_ERR_OOM;

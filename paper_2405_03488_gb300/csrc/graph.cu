@@ -10,12 +10,44 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "device.cuh"
 #include "internal.h"
 
 namespace gpm {
+
+static cudaMemPool_t g_pools[64];
+static std::once_flag g_pool_once[64];
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, st);
+    std::call_once(g_pool_once[dev], [dev]() {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = pool;
+    });
+    if (!g_pools[dev]) return cudaMallocAsync(p, bytes, st);
+    return cudaMallocFromPoolAsync(p, bytes, g_pools[dev], st);
+}
+
+void pool_free(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
 
 thread_local std::string g_last_error;
 
@@ -261,8 +293,8 @@ extern "C" gpm_status gpm_load_csr(uint64_t n, const uint64_t *row_ptr, const ui
         g->d.col = col;
     } else {
         nnz = row_ptr[n];
-        if (cudaMalloc((void **)&g->own_row_ptr, sizeof(uint64_t) * (n + 1)) != cudaSuccess ||
-            cudaMalloc((void **)&g->own_col, sizeof(uint32_t) * (nnz ? nnz : 1)) != cudaSuccess) {
+        if (pool_alloc((void **)&g->own_row_ptr, sizeof(uint64_t) * (n + 1), st) != cudaSuccess ||
+            pool_alloc((void **)&g->own_col, sizeof(uint32_t) * (nnz ? nnz : 1), st) != cudaSuccess) {
             set_error("gpm_load_csr: device allocation failed");
             return fail(GPM_ERR_OOM);
         }
@@ -278,10 +310,10 @@ extern "C" gpm_status gpm_load_csr(uint64_t n, const uint64_t *row_ptr, const ui
     }
     g->d.n = n;
     g->d.nnz = nnz;
-    if (cudaMalloc((void **)&g->up, sizeof(uint64_t) * (n + 1)) != cudaSuccess ||
-        cudaMalloc((void **)&g->uoff, sizeof(uint64_t) * (n + 1)) != cudaSuccess ||
-        cudaMalloc((void **)&g->totals, sizeof(Totals) * 2) != cudaSuccess ||
-        cudaMalloc((void **)&g->counter, sizeof(unsigned int) * 64) != cudaSuccess ||
+    if (pool_alloc((void **)&g->up, sizeof(uint64_t) * (n + 1), st) != cudaSuccess ||
+        pool_alloc((void **)&g->uoff, sizeof(uint64_t) * (n + 1), st) != cudaSuccess ||
+        pool_alloc((void **)&g->totals, sizeof(Totals) * 2, st) != cudaSuccess ||
+        pool_alloc((void **)&g->counter, sizeof(unsigned int) * 64, st) != cudaSuccess ||
         cudaMallocHost((void **)&g->totals_host, sizeof(Totals) * 2) != cudaSuccess) {
         set_error("gpm_load_csr: device allocation failed");
         return fail(GPM_ERR_OOM);
@@ -292,9 +324,9 @@ extern "C" gpm_status gpm_load_csr(uint64_t n, const uint64_t *row_ptr, const ui
     }
     unsigned int *bad = nullptr;
     unsigned long long *maxd = nullptr;
-    if (cudaMalloc((void **)&bad, sizeof(unsigned int)) != cudaSuccess ||
-        cudaMalloc((void **)&maxd, sizeof(unsigned long long)) != cudaSuccess) {
-        cudaFree(bad);
+    if (pool_alloc((void **)&bad, sizeof(unsigned int), st) != cudaSuccess ||
+        pool_alloc((void **)&maxd, sizeof(unsigned long long), st) != cudaSuccess) {
+        pool_free(bad, st);
         set_error("gpm_load_csr: device allocation failed");
         return fail(GPM_ERR_OOM);
     }
@@ -310,8 +342,8 @@ extern "C" gpm_status gpm_load_csr(uint64_t n, const uint64_t *row_ptr, const ui
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_h, bad, sizeof(bad_h), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && bad_h != 0xFF) {
-        cudaFree(bad);
-        cudaFree(maxd);
+        pool_free(bad, st);
+        pool_free(maxd, st);
         set_error(std::string("gpm_load_csr: invalid CSR: ") + kValidateMsg[bad_h < 6 ? bad_h : 0]);
         return fail(GPM_ERR_GRAPH);
     }
@@ -333,8 +365,8 @@ extern "C" gpm_status gpm_load_csr(uint64_t n, const uint64_t *row_ptr, const ui
     if (e == cudaSuccess) e = cudaMemcpyAsync(&maxd_h, maxd, sizeof(maxd_h), cudaMemcpyDeviceToHost, st);
     if (cnt) cudaFreeAsync(cnt, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(bad);
-    cudaFree(maxd);
+    pool_free(bad, st);
+    pool_free(maxd, st);
     if (e != cudaSuccess) {
         set_error(std::string("gpm_load_csr: ") + cudaGetErrorString(e));
         return fail(GPM_ERR_CUDA);
@@ -345,7 +377,7 @@ extern "C" gpm_status gpm_load_csr(uint64_t n, const uint64_t *row_ptr, const ui
     g->max_degree = maxd_h;
     // optional first-edge table; without memory for it the sampler searches uoff
     g->d.edges = nullptr;
-    if (m > 0 && cudaMalloc((void **)&g->edges, sizeof(uint64_t) * m) == cudaSuccess) {
+    if (m > 0 && pool_alloc((void **)&g->edges, sizeof(uint64_t) * m, st) == cudaSuccess) {
         const uint64_t warps = n < (1ull << 22) ? n : (1ull << 22);
         oriented_edges<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(g->d.row_ptr, g->d.col, g->up, g->uoff,
                                                                              n, g->edges);
@@ -368,14 +400,14 @@ extern "C" void gpm_free_graph(gpm_graph *g) {
     if (!g) return;
     if (g->stream) cudaStreamSynchronize(g->stream);
     else cudaDeviceSynchronize();
-    cudaFree(g->own_row_ptr);
-    cudaFree(g->own_col);
-    cudaFree(g->up);
-    cudaFree(g->uoff);
-    cudaFree(g->edges);
-    cudaFree(g->partials);
-    cudaFree(g->totals);
-    cudaFree(g->counter);
+    pool_free(g->own_row_ptr, g->stream);
+    pool_free(g->own_col, g->stream);
+    pool_free(g->up, g->stream);
+    pool_free(g->uoff, g->stream);
+    pool_free(g->edges, g->stream);
+    pool_free(g->partials, g->stream);
+    pool_free(g->totals, g->stream);
+    pool_free(g->counter, g->stream);
     if (g->totals_host) cudaFreeHost(g->totals_host);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);

@@ -55,6 +55,12 @@ struct Totals {
 
 void set_error(const std::string &msg);
 
+// Stream-ordered device allocations from the library's pool (one per device,
+// memory kept by the pool when freed, so a freed graph's arrays serve the next
+// graph loaded in the process without new device mappings).
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st);
+void pool_free(void *p, cudaStream_t st);
+
 // Single correctly rounded FP64 operations on host and device (the device
 // would otherwise be free to fuse a multiply and an add).
 __host__ __device__ inline double rn_add(double a, double b) {

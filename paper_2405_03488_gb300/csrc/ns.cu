@@ -172,10 +172,10 @@ static cudaError_t launch_ns(gpm_graph *h, const Plan &p, const Shape &sh, const
 
 static gpm_status ensure_partials(gpm_graph *h, uint64_t n) {
     if (h->partials_cap >= n) return GPM_OK;
-    cudaFree(h->partials);
+    pool_free(h->partials, h->stream);
     h->partials = nullptr;
     h->partials_cap = 0;
-    if (cudaMalloc((void **)&h->partials, sizeof(Partial) * n) != cudaSuccess) {
+    if (pool_alloc((void **)&h->partials, sizeof(Partial) * n, h->stream) != cudaSuccess) {
         set_error("device allocation of the per-chunk partials failed");
         return GPM_ERR_OOM;
     }
