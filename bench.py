@@ -582,9 +582,14 @@ def main():
     barrier()
     t0 = time.perf_counter()
     e2e_samples, e2e_d2h = 0, 0
+    t_load, t_est = [], []
     for s in range(args.steps):
+        ta = time.perf_counter()
         gh = api.Graph(rp_h.numpy().view(np.uint64), col_h.numpy().view(np.uint32))
+        tb = time.perf_counter()
         r = one_step(gh, s)
+        t_load.append(tb - ta)
+        t_est.append(time.perf_counter() - tb)
         gh.close()
         e2e_samples += sum(r[p]["samples"] for p in PATTERNS)
         # per graph launch the control word (16 B) comes back, at the end the job states
@@ -592,7 +597,8 @@ def main():
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
     e2e = {"value": e2e_samples * world / e2e_t, "unit": "samples/s",
-           "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz, "d2h_bytes_per_step": e2e_d2h // args.steps}
+           "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz, "d2h_bytes_per_step": e2e_d2h // args.steps,
+           "load_ms_per_step": [1e3 * x for x in t_load], "estimate_ms_per_step": [1e3 * x for x in t_est]}
 
     learned = learned_vs_plain(g, api) if (rank == 0 and not args.no_learned) else None
     if rank != 0:
@@ -627,6 +633,15 @@ def main():
         roof.update({"achieved": achieved, "frac": achieved / peak if peak else None,
                      "bytes_per_sample": bbar, "launches": int(rounds),
                      "avg_launch_ms": 1e3 * kernel_s / max(1, rounds)})
+        # the random-access roofline of the same pattern: dependent chains of 32-byte
+        # sector reads over a buffer the size of the CSR (secondary to the copy peak)
+        csr = 8 * (n + 1) + 4 * nnz
+        gather = {"buffer_bytes": csr}
+        for chain in (3, 6):
+            r_rand = api.gather_probe(csr, chain=chain) / 1e9
+            gather["chain%d_GBps" % chain] = r_rand
+            gather["frac_chain%d" % chain] = achieved / r_rand
+        roof["gather_roofline"] = gather
     line["roofline"] = roof
     print(json.dumps(line))
 

@@ -354,6 +354,16 @@ gpm_status gpm_sparsify(gpm_graph *g, uint32_t colors, uint64_t seed, uint32_t c
 gpm_status gpm_sparsify_edges(gpm_graph *g, double p, uint64_t seed, uint32_t colouring, uint32_t slot,
                               uint64_t *row_out, uint32_t *col_out, uint64_t *kept);
 
+/* Measurement only (not part of any estimate): the random-access roofline
+ * of the sampler's memory pattern.  Threads follow independent chains of
+ * `chain` dependent hops through a fresh buffer of `bytes` random words; each
+ * hop reads one 32-byte sector at a random position computed from the
+ * previous hop's data.  About `hops` hops are timed (after one warm-up pass)
+ * and *sectors_bytes_per_s receives 32 bytes x hops / kernel time.  Use a
+ * buffer the size of the graph (an L2-resident size gives the L2 figure).
+ * bytes >= 4096, 1 <= chain <= 64. */
+gpm_status gpm_gather_probe(uint64_t bytes, uint32_t chain, uint64_t hops, double *sectors_bytes_per_s);
+
 /* Ask a running estimate on this handle to stop at its next round boundary
  * (it returns GPM_ERR_ABORTED with the partial result). */
 gpm_status gpm_abort(gpm_graph *g);

@@ -115,6 +115,7 @@ SIGNATURES = [
     ("gpm_sparsify", _i32, [_V, _u32, _u64, _u32, _u32, _V, _V, P(_u64)]),
     ("gpm_sparsify_edges", _i32, [_V, _dbl, _u64, _u32, _u32, _V, _V, P(_u64)]),
     ("gpm_abort", _i32, [_V]),
+    ("gpm_gather_probe", _i32, [_u64, _u32, _u64, P(_dbl)]),
     ("gpm_plan", _i32, [P(Pattern), P(_i32), P(_i32), P(_i32), P(_i32), P(_i32)]),
     ("gpm_normal_quantile", _dbl, [_dbl]),
     ("gpm_last_error", C.c_char_p, []),

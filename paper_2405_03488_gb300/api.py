@@ -201,6 +201,14 @@ class Graph:
         check(_lib.load().gpm_abort(self.h), "gpm_abort")
 
 
+def gather_probe(nbytes, chain=4, hops=1 << 28):
+    """Random 32-byte-sector gather throughput (bytes/s) over a buffer of nbytes,
+    chains of `chain` dependent hops (the sampler's access pattern)."""
+    out = C.c_double()
+    check(_lib.load().gpm_gather_probe(nbytes, chain, hops, C.byref(out)), "gpm_gather_probe")
+    return out.value
+
+
 def plan(pat):
     """(order, restrictions, oriented) from the library's host planner."""
     pp = pattern(pat)

@@ -58,3 +58,4 @@ def test_sharded_estimate_equals_single_gpu(graph, name, world):
     one = graph.estimate(name, eps=eps, delta=0.01, seed=seed, window=W, slot=slot)
     for f in ("estimate", "ci_half_width", "eps_hat", "samples", "hits", "rounds", "converged", "sum", "sumsq"):
         assert res[f] == one[f], f
+
