@@ -301,6 +301,18 @@ def companion(args):
         out.update({"n": g.n, "m": g.m, "samples": s.n, "seconds": t, "samples_per_s": s.n / t,
                     "estimate": mu, "exact": exact, "rel_err": abs(mu - exact) / exact, "z": (mu - exact) / sd,
                     "hit_rate": s.hits / s.n, "eps_hat_99": 2.5758293035489004 * sd / mu})
+        # empirical coverage of the convergence test: seeds 1..1000 at +-5% / 95% and +-1% / 99%
+        cov = {}
+        for eps, delta, R in ((0.05, 0.05, 1000), (0.01, 0.01, 1000)):
+            miss, samples, tt = 0, 0, 0.0
+            for sd_ in range(1, R + 1):
+                r, ts = _timed(lambda: g.estimate("triangle", eps=eps, delta=delta, seed=sd_, window=1 << 16))
+                miss += abs(r["estimate"] - exact) > eps * exact
+                samples += r["samples"]
+                tt += ts
+            cov["eps%g_delta%g" % (eps, delta)] = {"runs": R, "within_eps": 1 - miss / R, "nominal": 1 - delta,
+                                                   "mean_samples": samples / R, "mean_time_to_converge_s": tt / R}
+        out["coverage"] = cov
     elif args.config == "rmat24-batch":
         # one batched run: 6 connected 4-vertex motifs (vertex-induced) and triangles, eps 0.5/1/2 %
         rp, col = G.rmat(24, 16, seed=3, device="cuda")

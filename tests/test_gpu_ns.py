@@ -175,3 +175,21 @@ def test_rmat22_sampled_parity_in_bench_shape(rmat22, name):
     acc, _ = O.ns_run(og, p, seed=1, first=1 << 20, count=1 << 18)
     assert (s.n, s.hits) == (acc.n, acc.hits)
     assert s.sum == pytest.approx(acc.sum, rel=REL) and s.sumsq == pytest.approx(acc.sumsq, rel=REL)
+
+
+def test_interval_coverage_on_er_triangles():
+    """1000 seeds of the convergence test on G(10^4, 0.002) triangles (the
+    exact count from the exact counter, checked against the oracle): the
+    fraction of stopped estimates within eps of C is at least 1 - delta minus
+    three binomial standard deviations."""
+    rp, col = G.erdos_renyi(10_000, 0.002, seed=1)
+    g, og = pair(rp, col)
+    C = g.exact_count("triangle")
+    assert C == O.exact_count(og, O.plan(*G.pattern("triangle")))
+    R, eps, delta = 1000, 0.05, 0.05
+    miss = 0
+    for s in range(1, R + 1):
+        r = g.estimate("triangle", eps=eps, delta=delta, seed=s, window=1 << 14)
+        assert r["converged"] == 1
+        miss += abs(r["estimate"] - C) > eps * C
+    assert miss <= R * delta + 3 * (R * delta * (1 - delta)) ** 0.5, miss

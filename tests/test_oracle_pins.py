@@ -364,6 +364,24 @@ def test_online_window_and_stop_rule():
     assert out2.converged == 0 and out2.samples == 3 * W
 
 
+def test_online_interval_coverage_over_seeds():
+    """Empirical coverage of the convergence test (Algorithm 3, Theorem 1): over
+    400 seeds the stopped estimate misses C by more than eps C in at most
+    delta R runs plus three binomial standard deviations."""
+    rp, col = G.erdos_renyi(300, 0.08, seed=21)
+    g = og(rp, col)
+    R, eps, delta, W = 400, 0.1, 0.05, 1 << 9
+    for name in ("triangle", "4-cycle"):
+        p = O.plan(*G.pattern(name))
+        C = O.exact_count(g, p)
+        miss = 0
+        for s in range(1, R + 1):
+            o = O.ns_online(g, p, eps, delta, seed=s, window=W)
+            assert o.converged == 1
+            miss += abs(o.estimate - C) > eps * C
+        assert miss <= R * delta + 3 * (R * delta * (1 - delta)) ** 0.5, (name, miss)
+
+
 # ------------------------------------------------------------------ GS
 def test_gs_one_colour_is_exact():
     rp, col = G.random_small(11, 0.5, 2)
