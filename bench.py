@@ -377,6 +377,15 @@ def companion(args):
                 row[variant + "_hit_rate"] = sm.hits / sm.n
             out[name] = row
     elif args.config == "rmat27":
+        # the NS/GS selector head, trained on the timed small-graph cases first
+        (rows_s, labels_s, _, handles), t_cases = _timed(lambda: timed_selector_cases(api, G))
+        (sel, sel_loss), t_train = _timed(lambda: train_selector(api, rows_s, labels_s, next(iter(handles.values()))))
+        out["selector"] = {"cases": len(rows_s), "gs_faster": int(sum(labels_s)), "cases_s": t_cases,
+                           "train_s": t_train, "train_loss": sel_loss}
+        for h_ in handles.values():
+            h_.close()
+        del handles
+        torch.cuda.empty_cache()
         # R-MAT scale 27, edge factor 16: about 2.1 billion undirected edges
         rp, col = G.rmat(27, 16, seed=5, device="cuda")
         torch.cuda.synchronize()
@@ -388,6 +397,11 @@ def companion(args):
                                              max_seconds=120.0))
             row = {"ns": {"seconds": t, "estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"],
                           "samples_per_s": r["samples"] / max(r["t_sample_s"], 1e-12), "converged": r["converged"]}}
+            for label, kw in (("hybrid_cost_model", {}), ("hybrid_selector", {"selector": sel})):
+                r, t = _timed(lambda: g.estimate(name, scheme=api.HYBRID, eps=EPS, delta=DELTA, seed=1, window=WINDOW,
+                                                 n_max=1 << 34, max_seconds=120.0, colors=8, **kw))
+                row[label] = {"seconds": t, "engine": "GS" if r["scheme_used"] == api.GS else "NS",
+                              "estimate": r["estimate"], "pilot_s": r["t_pilot_s"], "converged": r["converged"]}
             if name.endswith("clique"):
                 prop = api.Proposal(seed=1)
                 (loss, rows), ttrain = _timed(lambda: prop.train(g, name, seed=11, samples=1 << 20, epochs=2,
@@ -446,11 +460,9 @@ def selector_cases(G, device="cuda"):
     return [(gname, rc, p, c) for gname, rc in graphs.items() for p in pats for c in (4, 8)]
 
 
-def selector_study(api, G, eps=0.05, delta=0.01, time_cap=10.0):
-    """Label each case by which engine finished first (NS to eps at 1-delta, or
-    one GS colouring), train the selector head on every other case, and compare
-    its choices with the cost-model rule on the held-out cases."""
-    import torch
+def timed_selector_cases(api, G, eps=0.05, delta=0.01, time_cap=10.0):
+    """Selector features of each case and which engine finished first (NS to
+    eps at 1-delta, or one GS colouring)."""
     rows, labels, meta = [], [], []
     handles = {}
     for gname, (rp, col), pname, c in selector_cases(G):
@@ -467,6 +479,23 @@ def selector_study(api, G, eps=0.05, delta=0.01, time_cap=10.0):
         labels.append(1.0 if t_gs < t_ns else 0.0)
         meta.append({"graph": gname, "pattern": pname, "colors": c, "t_ns": t_ns, "t_gs": t_gs,
                      "cost_model_gs": info["cost_model_gs"]})
+    return rows, labels, meta, handles
+
+
+def train_selector(api, rows, labels, handle):
+    import torch
+    feat = torch.tensor(rows, dtype=torch.float32, device="cuda")
+    lab = torch.tensor(labels, dtype=torch.float32, device="cuda")
+    sel = api.Proposal(seed=2)
+    loss = sel.train_rows(handle, feat, lab, epochs=400, batch=64, lr=1e-2)
+    return sel, loss
+
+
+def selector_study(api, G, eps=0.05, delta=0.01, time_cap=10.0):
+    """Train the selector head on every other timed case and compare its choices
+    with the cost-model rule on the held-out cases."""
+    import torch
+    rows, labels, meta, handles = timed_selector_cases(api, G, eps, delta, time_cap)
     feat = torch.tensor(rows, dtype=torch.float32, device="cuda")
     lab = torch.tensor(labels, dtype=torch.float32, device="cuda")
     n = len(rows)
