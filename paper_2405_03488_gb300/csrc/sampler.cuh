@@ -32,7 +32,9 @@ constexpr uint32_t kLearnedMax = 256;   // larger candidate sets are drawn unifo
 #endif
 constexpr int kMlpFloats = 4481;        // 3->64->64->1 weights and biases
 constexpr int kMlpSmemFloats = 4482;    // padded to 8 bytes
-constexpr int kLearnedWarpWords = 128 + kLearnedMax;   // hidden activations + scores
+// hidden activations, scores, and each candidate's CSR offsets (u64 row start,
+// u32 degree, u32 offset of its first neighbour above itself)
+constexpr int kLearnedWarpWords = 128 + kLearnedMax + 4 * kLearnedMax;
 
 struct RunArgs {
     uint64_t seed;
@@ -186,11 +188,10 @@ __device__ __forceinline__ uint32_t mlp_score(const WarpMem &wm, float f0, float
 template <typename PlanT>
 static __device__ __noinline__ uint64_t lookahead_count(const DGraph &g, const PlanT &p, const WarpMem &wm,
                                                  const uint32_t *Sj, uint32_t sz, uint32_t ix, int j, uint64_t lb,
-                                                 uint64_t le) {
+                                                 uint64_t le, uint64_t xb, uint64_t xe, uint64_t xu) {
     const unsigned lane = lane_id();
     const int jj = j + 1;
     const uint32_t x = Sj[ix];
-    const uint64_t xb = __ldg(g.row_ptr + x), xe = __ldg(g.row_ptr + x + 1), xu = __ldg(g.up + x);
     const uint32_t lm = p.lower[jj];
     const bool has_lo = lm != 0;
     uint32_t lo = 0;
@@ -201,8 +202,12 @@ static __device__ __noinline__ uint64_t lookahead_count(const DGraph &g, const P
         }
     uint64_t cnt = 0;
     if (p.reuse[jj] == 1) {
+        // entries of S_j at or below the bound (S_j ascends, so with the bound
+        // at x itself they are the first ix + 1)
         uint32_t s0 = 0;
-        if (has_lo)
+        if (has_lo && lo == x)
+            s0 = ix + 1;
+        else if (has_lo)
             for (uint32_t base = 0; base < sz; base += 32) {
                 const uint32_t idx = base + lane;
                 s0 += __popc(__ballot_sync(kFull, idx < sz && Sj[idx] <= lo));
@@ -263,11 +268,21 @@ static __device__ __noinline__ uint32_t learned_pick(const DGraph &g, const Plan
                                               uint32_t sz, int j, uint64_t r, uint64_t lb, uint64_t le,
                                               uint64_t *A_out, uint32_t *a_out) {
     const unsigned lane = lane_id();
+    // every candidate's CSR offsets in one pass over the lanes
+    uint64_t *cb = reinterpret_cast<uint64_t *>(wm.score + kLearnedMax);
+    uint32_t *cd = wm.score + 3 * kLearnedMax, *cu = wm.score + 4 * kLearnedMax;
+    for (uint32_t i = lane; i < sz; i += 32) {
+        const uint32_t x = Sj[i];
+        const uint64_t xb = __ldg(g.row_ptr + x);
+        cb[i] = xb;
+        cd[i] = (uint32_t)(__ldg(g.row_ptr + x + 1) - xb);
+        cu[i] = (uint32_t)(__ldg(g.up + x) - xb);
+    }
+    __syncwarp();
     uint64_t A = 0;
     for (uint32_t i = 0; i < sz; i++) {
-        const uint32_t x = Sj[i];
-        const uint64_t nxt = lookahead_count(g, p, wm, Sj, sz, i, j, lb, le);
-        const uint64_t dx = __ldg(g.row_ptr + x + 1) - __ldg(g.row_ptr + x);
+        const uint64_t xb = cb[i], dx = cd[i];
+        const uint64_t nxt = lookahead_count(g, p, wm, Sj, sz, i, j, lb, le, xb, xb + dx, xb + cu[i]);
         const uint32_t a = mlp_score(wm, flog2p1(dx), __int2float_rn(j), flog2p1(nxt));
         if (lane == 0) wm.score[i] = a;
         A += a;
