@@ -2,6 +2,8 @@
 // batched kernels.  See ns.cu for the method and the layout.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,6 +32,7 @@ constexpr uint32_t kLearnedMax = 256;   // larger candidate sets are drawn unifo
 #ifndef GPM_REUSE_STREAM_BIAS
 #define GPM_REUSE_STREAM_BIAS 0
 #endif
+
 constexpr int kMlpFloats = 4481;        // 3->64->64->1 weights and biases
 constexpr int kMlpSmemFloats = 4482;    // padded to 8 bytes
 // hidden activations, scores, and each candidate's CSR offsets (u64 row start,
@@ -321,6 +324,9 @@ struct SampleOut {
 
 template <int MODE, typename PlanT>
 __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &a, uint64_t s, WarpMem &wm) {
+    // the batched kernel (plan copy in shared memory) runs faster with one
+    // inlined copy of the step-2 predicate, the single-run kernel with four
+    constexpr bool kCompact = std::is_same<PlanT, StepPlan>::value;
     const unsigned lane = lane_id();
     const int k = p.k;
     SampleOut out;
@@ -586,6 +592,21 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                             const uint64_t idx = base + 32 * u + lane;
                             y[u] = idx < de ? __ldg(g.col + idx) : 0u;
                         }
+                        if constexpr (kCompact) {
+                        // one copy of pred: the element is picked by selects
+#pragma unroll 1
+                        for (int u = 0; u < 4; u++) {
+                            if (base + 32 * u >= de) break;
+                            const uint32_t yu = u == 0 ? y[0] : u == 1 ? y[1] : u == 2 ? y[2] : y[3];
+                            const bool ok = pred(yu) && (base + 32 * u + lane < de);
+                            const unsigned m = __ballot_sync(kFull, ok);
+                            if (ok) {
+                                const uint64_t pos = count + __popc(m & lanemask_lt());
+                                if (pos < a.cap) Sc[pos] = yu;
+                            }
+                            count += __popc(m);
+                        }
+                        } else {
 #pragma unroll
                         for (int u = 0; u < 4; u++) {
                             if (base + 32 * u >= de) break;
@@ -597,34 +618,67 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                             }
                             count += __popc(m);
                         }
+                        }
                     }
                     mat = count <= a.cap;
                     if (!mat) {
+                        if constexpr (kCompact) {
                         // second pass: locate the drawn element without storing the set
-                        const uint64_t target = index_map(r, count);
-                        uint64_t seen = 0;
-                        bool found = false;
-                        for (uint64_t base = dstart; base < de && !found; base += 128) {
-                            uint32_t y[4];
-#pragma unroll
-                            for (int u = 0; u < 4; u++) {
-                                const uint64_t idx = base + 32 * u + lane;
-                                y[u] = idx < de ? __ldg(g.col + idx) : 0u;
-                            }
-#pragma unroll
-                            for (int u = 0; u < 4; u++) {
-                                if (found || base + 32 * u >= de) break;
-                                const bool ok = pred(y[u]) && (base + 32 * u + lane < de);
-                                const unsigned m = __ballot_sync(kFull, ok);
-                                const uint64_t c = __popc(m);
-                                if (seen + c > target) {
-                                    const uint32_t rank = (uint32_t)(target - seen);
-                                    const bool mine = ok && (uint32_t)__popc(m & lanemask_lt()) == rank;
-                                    const int src = __ffs(__ballot_sync(kFull, mine)) - 1;
-                                    x = __shfl_sync(kFull, y[u], src);
-                                    found = true;
+                            const uint64_t target = index_map(r, count);
+                            uint64_t seen = 0;
+                            bool found = false;
+                            for (uint64_t base = dstart; base < de && !found; base += 128) {
+                                uint32_t y[4];
+    #pragma unroll
+                                for (int u = 0; u < 4; u++) {
+                                    const uint64_t idx = base + 32 * u + lane;
+                                    y[u] = idx < de ? __ldg(g.col + idx) : 0u;
                                 }
-                                seen += c;
+    #pragma unroll 1
+                                for (int u = 0; u < 4; u++) {
+                                    if (found || base + 32 * u >= de) break;
+                                    const uint32_t yu = u == 0 ? y[0] : u == 1 ? y[1] : u == 2 ? y[2] : y[3];
+                                    const bool ok = pred(yu) && (base + 32 * u + lane < de);
+                                    const unsigned m = __ballot_sync(kFull, ok);
+                                    const uint64_t c = __popc(m);
+                                    if (seen + c > target) {
+                                        const uint32_t rank = (uint32_t)(target - seen);
+                                        const bool mine = ok && (uint32_t)__popc(m & lanemask_lt()) == rank;
+                                        const int src = __ffs(__ballot_sync(kFull, mine)) - 1;
+                                        x = __shfl_sync(kFull, yu, src);
+                                        found = true;
+                                    }
+                                    seen += c;
+                                }
+                            }
+                        } else {
+                        // second pass: locate the drawn element without storing the set
+                            const uint64_t target = index_map(r, count);
+                            uint64_t seen = 0;
+                            bool found = false;
+                            for (uint64_t base = dstart; base < de && !found; base += 128) {
+                                uint32_t y[4];
+    #pragma unroll
+                                for (int u = 0; u < 4; u++) {
+                                    const uint64_t idx = base + 32 * u + lane;
+                                    y[u] = idx < de ? __ldg(g.col + idx) : 0u;
+                                }
+    #pragma unroll
+                                for (int u = 0; u < 4; u++) {
+                                    if (found || base + 32 * u >= de) break;
+                                    const uint32_t yu = y[u];
+                                    const bool ok = pred(yu) && (base + 32 * u + lane < de);
+                                    const unsigned m = __ballot_sync(kFull, ok);
+                                    const uint64_t c = __popc(m);
+                                    if (seen + c > target) {
+                                        const uint32_t rank = (uint32_t)(target - seen);
+                                        const bool mine = ok && (uint32_t)__popc(m & lanemask_lt()) == rank;
+                                        const int src = __ffs(__ballot_sync(kFull, mine)) - 1;
+                                        x = __shfl_sync(kFull, yu, src);
+                                        found = true;
+                                    }
+                                    seen += c;
+                                }
                             }
                         }
                     }
