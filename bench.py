@@ -660,7 +660,7 @@ def main():
 
     peak, peak_kind = measured_peaks()
     roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
-            "traffic": ncu_traffic(), "kernel": "ns_batch_kernel<INTERSECT>", "peak_kind": peak_kind}
+            "traffic": ncu_traffic(), "kernel": "ns_batch_kernel<INTERSECT, compact>", "peak_kind": peak_kind}
     if world == 1 and not args.no_cpu_baseline:
         ores, wall, cores = oracle_sample(*G.to_numpy(rp, col), args.cpu_seconds)
         cpu_n = sum(v["n"] for v in ores.values())

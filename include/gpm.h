@@ -94,7 +94,8 @@ typedef struct {
     uint32_t block_warps;
     uint32_t cap;           /* per-warp on-chip candidate buffer, entries (0 = the largest
                                that keeps 4 resident 256-thread blocks per SM, 2 with a
-                               learned proposal; 832 at 8 warps on a GB300) */
+                               learned proposal, 832 at 8 warps on a GB300; at most 512
+                               when a pattern is vertex-induced) */
     const gpm_mlp *mlp;     /* learned proposal weights (device); required by GPM_NS_LEARNED and,
                                when set, selects the learned proposal in gpm_sample_sums,
                                gpm_sample_sums_static and gpm_trace */

@@ -51,7 +51,7 @@ struct BatchArgs {
 // static shared memory of ns_batch_kernel: one StepPlan per warp
 constexpr size_t kBatchStaticSmem = 8 * sizeof(StepPlan);
 
-template <int MODE>
+template <int MODE, bool COMPACT>
 __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOCKS)
     ns_batch_kernel(const DGraph g, const Plan *__restrict__ plans, const BatchJob *jobs, BatchCtl *ctl,
                     const BatchArgs ba, Partial *partials) {
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOC
         uint64_t hits = 0;
         for (uint64_t s = s0; s < s1; s++) {
             __syncwarp();
-            const SampleOut r = sample_one<MODE>(g, p, a, s, wm);
+            const SampleOut r = sample_one<MODE, StepPlan, COMPACT>(g, p, a, s, wm);
             if (r.hit) {
                 sum = __dadd_rn(sum, r.w);
                 sumsq = __dadd_rn(sumsq, __dmul_rn(r.w, r.w));
@@ -182,9 +182,9 @@ __global__ void batch_relayout(BatchJob *jobs, BatchCtl *ctl, const BatchArgs ba
     ctl->rounds += 1;
 }
 
-template <int MODE>
+template <int MODE, bool COMPACT>
 static cudaError_t batch_grid(gpm_graph *h, const Shape &sh, uint32_t *blocks) {
-    auto kern = ns_batch_kernel<MODE>;
+    auto kern = ns_batch_kernel<MODE, COMPACT>;
     const size_t smem = smem_bytes(sh, MODE);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -222,7 +222,11 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
     bool single = false;
     for (const Plan &pl : plans) single = single || plan_single_steps(pl);
     const int kmode = kernel_mode(mode, single);
-    if (sh.cap == 0) sh.cap = fit_cap(h, kBatchStaticSmem, sh.warps, mode);
+    bool induced = false;
+    for (const Plan &pl : plans) induced = induced || pl.induced;
+    // the compact step-2 loop for edge-induced batches (see sample_one)
+    const bool compact = !induced && (kmode == MODE_INTERSECT || kmode == MODE_INTERSECT_SINGLE);
+    if (sh.cap == 0) sh.cap = default_cap(h, kBatchStaticSmem, sh.warps, mode, induced);
     if (mode == MODE_LEARNED && sh.cap < kLearnedMax) sh.cap = kLearnedMax;
     const uint64_t cpj = (W + sh.chunk - 1) / sh.chunk;
     if (cpj * nj >= (1ull << 31)) {
@@ -306,10 +310,13 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
     uint32_t blocks = 0;
     if (e == cudaSuccess)
-        e = (kmode == MODE_CHECK)              ? batch_grid<MODE_CHECK>(h, sh, &blocks)
-            : (kmode == MODE_LEARNED)          ? batch_grid<MODE_LEARNED>(h, sh, &blocks)
-            : (kmode == MODE_INTERSECT_SINGLE) ? batch_grid<MODE_INTERSECT_SINGLE>(h, sh, &blocks)
-                                               : batch_grid<MODE_INTERSECT>(h, sh, &blocks);
+        e = (kmode == MODE_CHECK)     ? batch_grid<MODE_CHECK, false>(h, sh, &blocks)
+            : (kmode == MODE_LEARNED) ? batch_grid<MODE_LEARNED, false>(h, sh, &blocks)
+            : (kmode == MODE_INTERSECT_SINGLE)
+                ? (compact ? batch_grid<MODE_INTERSECT_SINGLE, true>(h, sh, &blocks)
+                           : batch_grid<MODE_INTERSECT_SINGLE, false>(h, sh, &blocks))
+                : (compact ? batch_grid<MODE_INTERSECT, true>(h, sh, &blocks)
+                           : batch_grid<MODE_INTERSECT, false>(h, sh, &blocks));
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         const size_t smem = smem_bytes(sh, mode);
@@ -317,15 +324,22 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
             // event nodes around each sampler launch time the sampler alone
             cudaEventRecordWithFlags(ev_k[2 * r], cs, cudaEventRecordExternal);
             if (kmode == MODE_CHECK)
-                ns_batch_kernel<MODE_CHECK><<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
+                ns_batch_kernel<MODE_CHECK, false>
+                    <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
             else if (kmode == MODE_LEARNED)
-                ns_batch_kernel<MODE_LEARNED>
+                ns_batch_kernel<MODE_LEARNED, false>
+                    <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
+            else if (kmode == MODE_INTERSECT_SINGLE && compact)
+                ns_batch_kernel<MODE_INTERSECT_SINGLE, true>
                     <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
             else if (kmode == MODE_INTERSECT_SINGLE)
-                ns_batch_kernel<MODE_INTERSECT_SINGLE>
+                ns_batch_kernel<MODE_INTERSECT_SINGLE, false>
+                    <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
+            else if (compact)
+                ns_batch_kernel<MODE_INTERSECT, true>
                     <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
             else
-                ns_batch_kernel<MODE_INTERSECT>
+                ns_batch_kernel<MODE_INTERSECT, false>
                     <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
             cudaEventRecordWithFlags(ev_k[2 * r + 1], cs, cudaEventRecordExternal);
             batch_reduce_check<<<nj, 1024, 0, cs>>>(d_parts, d_jobs, ba);
@@ -474,7 +488,9 @@ extern "C" gpm_status gpm_autotune(gpm_graph *h, uint32_t count, const gpm_patte
         }
     }
     io->block_warps = bw;
-    io->cap = bc ? bc : fit_cap(h, kBatchStaticSmem, bw, MODE_INTERSECT);
+    bool induced = false;
+    for (const Plan &pl : plans) induced = induced || pl.induced;
+    io->cap = bc ? bc : default_cap(h, kBatchStaticSmem, bw, MODE_INTERSECT, induced);
     set_error("");
     return GPM_OK;
 }

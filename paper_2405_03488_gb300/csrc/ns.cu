@@ -191,7 +191,7 @@ static gpm_status run_block(gpm_graph *h, const Plan &p, int mode, uint64_t seed
                             uint64_t count, const gpm_config *cfg, int accumulate, gpm_sample_record *trace,
                             float *kernel_ms, uint32_t rank = 0, uint32_t world = 1, uint64_t *nchunks_out = nullptr) {
     Shape sh = pick_shape(h, cfg, count);
-    if (sh.cap == 0) sh.cap = fit_cap(h, 0, sh.warps, mode);   // ns_kernel has no static shared memory
+    if (sh.cap == 0) sh.cap = default_cap(h, 0, sh.warps, mode, p.induced);   // ns_kernel: no static shared memory
     if (mode == MODE_LEARNED && sh.cap < kLearnedMax) sh.cap = kLearnedMax;
     const uint64_t all_chunks = (count + sh.chunk - 1) / sh.chunk;
     const uint64_t nchunks = (rank < all_chunks) ? (all_chunks - rank + world - 1) / world : 0;
@@ -803,7 +803,7 @@ extern "C" gpm_status gpm_sample_sums_static(gpm_graph *h, const gpm_pattern *pa
 
     Shape sh = pick_shape(h, cfg, count);
     const int mode = mode_of(cfg);
-    if (sh.cap == 0) sh.cap = fit_cap(h, 0, sh.warps, mode);
+    if (sh.cap == 0) sh.cap = default_cap(h, 0, sh.warps, mode, p.induced);
     if (mode == MODE_LEARNED && sh.cap < kLearnedMax) sh.cap = kLearnedMax;
     const uint64_t min_chunk = (count + kStaticMaxChunks - 1) / kStaticMaxChunks;
     if (sh.chunk < min_chunk) sh.chunk = (uint32_t)min_chunk;

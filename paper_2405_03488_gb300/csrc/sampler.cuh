@@ -322,11 +322,14 @@ struct SampleOut {
     bool hit, overflow;
 };
 
-template <int MODE, typename PlanT>
+// COMPACT: evaluate the step-2 predicate from one inlined copy (the element
+// picked by selects) instead of four unrolled copies.  Fewer instruction-fetch
+// stalls make it faster in the batched kernel for edge-induced plans; the
+// unrolled copies overlap the global searches of vertex-induced plans and
+// suit the single-run kernel.
+template <int MODE, typename PlanT, bool COMPACT = false>
 __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &a, uint64_t s, WarpMem &wm) {
-    // the batched kernel (plan copy in shared memory) runs faster with one
-    // inlined copy of the step-2 predicate, the single-run kernel with four
-    constexpr bool kCompact = std::is_same<PlanT, StepPlan>::value;
+    constexpr bool kCompact = COMPACT;
     const unsigned lane = lane_id();
     const int k = p.k;
     SampleOut out;
@@ -777,6 +780,14 @@ inline uint32_t fit_cap(const gpm_graph *h, size_t static_smem, uint32_t warps, 
     if (cap < 64) cap = 64;
     if (cap > 2048) cap = 2048;
     return (uint32_t)cap;
+}
+
+// Default buffer for a set of plans: vertex-induced plans test non-edges by
+// searches in global memory, which want the L1 capacity a larger shared-memory
+// carve-out takes, so they keep 512 entries; otherwise fit_cap.
+inline uint32_t default_cap(const gpm_graph *h, size_t static_smem, uint32_t warps, int mode, bool induced) {
+    const uint32_t fit = fit_cap(h, static_smem, warps, mode);
+    return (induced && mode != MODE_LEARNED && fit > 512) ? 512 : fit;
 }
 
 // Samples per chunk is fixed, so per-chunk partials (and every FP64 total
