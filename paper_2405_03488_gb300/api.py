@@ -110,7 +110,8 @@ class Graph:
         pp = pattern(pat)
         c = config(**cfg)
         code = _lib.load().gpm_estimate(self.h, C.byref(pp), scheme, eps, delta, seed, C.byref(c), C.byref(res))
-        ok = (_lib.GPM_OK, _lib.GPM_ERR_NOT_CONVERGED) if allow_unconverged else (_lib.GPM_OK,)
+        # NOT_CONVERGED and ABORTED still fill the result
+        ok = (_lib.GPM_OK, _lib.GPM_ERR_NOT_CONVERGED, _lib.GPM_ERR_ABORTED) if allow_unconverged else (_lib.GPM_OK,)
         check(code, "gpm_estimate", ok)
         d = res.as_dict()
         d["status"] = code

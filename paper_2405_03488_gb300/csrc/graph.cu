@@ -41,8 +41,13 @@ cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st) {
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
         g_pools[dev] = pool;
     });
-    if (!g_pools[dev]) return cudaMallocAsync(p, bytes, st);
-    return cudaMallocFromPoolAsync(p, bytes, g_pools[dev], st);
+    e = g_pools[dev] ? cudaMallocFromPoolAsync(p, bytes, g_pools[dev], st) : cudaMallocAsync(p, bytes, st);
+    if (e != cudaSuccess) {
+        // a refused allocation must not surface later as a launch error
+        cudaGetLastError();
+        *p = nullptr;
+    }
+    return e;
 }
 
 void pool_free(void *p, cudaStream_t st) {

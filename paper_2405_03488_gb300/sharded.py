@@ -65,23 +65,38 @@ def torch_gather(group=None):
     return gather
 
 
-def estimate_sharded(partials_fn, eps, delta, window, rank, world, gather, n_min=None, n_max=1 << 40):
+def estimate_sharded(partials_fn, eps, delta, window, rank, world, gather, n_min=None, n_max=1 << 40, state=None,
+                     max_rounds=None):
     """Algorithm 3 with each window's chunks split over ``world`` ranks.
 
     partials_fn(first, count, rank, world) returns this rank's chunk partials
     of samples [first, first + count) (``Graph.sample_partials`` with the
     pattern, seed and slot bound); gather(local) returns every rank's array in
-    rank order.  Returns the fields of a one-GPU estimate."""
+    rank order.  Returns the fields of a one-GPU estimate and, under "state",
+    the running window state.
+
+    Checkpoint and resume: ``max_rounds`` stops after that many windows of
+    this call; the returned state (a ``gpm_window``, 72 bytes, ``bytes(state)``
+    to save, ``_lib.Window.from_buffer_copy`` to load) passed back as ``state``
+    continues the run.  Window r always covers samples [r W, (r+1) W) of the
+    counter-based streams, so a resumed run equals the uninterrupted one bit
+    for bit."""
     if not (eps > 0 and 0 < delta < 1 and window > 0):
         raise ValueError("eps > 0, 0 < delta < 1 and window > 0 are required")
     z = _lib.load().gpm_normal_quantile(1.0 - delta / 2.0)
     n_min = window if n_min is None else n_min
-    st = _lib.Window()
-    st.active = 1
-    while st.active:
+    if state is None:
+        st = _lib.Window()
+        st.active = 1
+    else:
+        st = _lib.Window.from_buffer_copy(state)
+    done = 0
+    while st.active and (max_rounds is None or done < max_rounds):
         first = st.rounds * window
         local = partials_fn(first, window, rank, world)
         merged = merge_partials(interleave(gather(local)))
         window_update(st, merged, z, eps, n_min, n_max)
+        done += 1
     return {"estimate": st.mu, "ci_half_width": st.half, "eps_hat": st.eps_hat, "samples": st.n,
-            "hits": st.hits, "rounds": st.rounds, "converged": st.converged, "sum": st.sum, "sumsq": st.sumsq}
+            "hits": st.hits, "rounds": st.rounds, "converged": st.converged, "sum": st.sum, "sumsq": st.sumsq,
+            "active": st.active, "state": st}

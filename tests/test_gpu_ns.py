@@ -232,3 +232,28 @@ def test_rmat27_sampled_parity_at_full_size():
     acc, _ = O.ns_run(og, O.plan(*G.pattern("5-clique")), seed=1, first=1 << 30, count=1 << 15)
     assert (s.n, s.hits) == (acc.n, acc.hits)
     assert s.sum == pytest.approx(acc.sum, rel=REL) and s.sumsq == pytest.approx(acc.sumsq, rel=REL)
+
+
+def test_abort_deadline_and_allocation_failure_are_clean():
+    """Failure handling without faulting the GPU: an abort set from another
+    host thread ends a running estimate with ABORTED and a partial result;
+    max_seconds ends one with NOT_CONVERGED; a CSR too large for the device
+    fails with OOM before any copy; the handle stays usable after each."""
+    import threading
+    import time
+    from paper_2405_03488_gb300 import _lib
+    rp, col = G.rmat(16, 16, seed=3, device="cuda")
+    g = api.Graph(rp, col)
+    threading.Timer(0.3, g.abort).start()
+    t0 = time.perf_counter()
+    r = g.estimate("5-clique", eps=1e-5, delta=0.01, seed=1, window=1 << 16, n_max=1 << 40)
+    assert r["status"] == _lib.GPM_ERR_ABORTED and r["converged"] == 0 and r["samples"] > 0
+    assert time.perf_counter() - t0 < 30
+    r = g.estimate("5-clique", eps=1e-5, delta=0.01, seed=1, window=1 << 16, n_max=1 << 40, max_seconds=0.3)
+    assert r["status"] == _lib.GPM_ERR_NOT_CONVERGED and r["converged"] == 0 and r["samples"] > 0
+    big = np.array([0, 1 << 40], dtype=np.uint64)      # claims 2^40 neighbour entries
+    with pytest.raises(_lib.GpmError) as e:
+        api.Graph(big, np.zeros(4, dtype=np.uint32))
+    assert e.value.code == _lib.GPM_ERR_OOM
+    r = g.estimate("triangle", eps=0.05, delta=0.01, seed=2, window=1 << 16)
+    assert r["converged"] == 1

@@ -59,3 +59,15 @@ def test_sharded_estimate_equals_single_gpu(graph, name, world):
     for f in ("estimate", "ci_half_width", "eps_hat", "samples", "hits", "rounds", "converged", "sum", "sumsq"):
         assert res[f] == one[f], f
 
+
+
+def test_resumed_estimate_equals_single_gpu(graph):
+    seed, W = 8, 1 << 14
+    fn = lambda first, count, rank, world: graph.sample_partials("5-clique", seed, first, count, rank, world)
+    gather = lambda local: [local]
+    part = sharded.estimate_sharded(fn, 0.02, 0.01, W, 0, 1, gather, max_rounds=1)
+    rest = sharded.estimate_sharded(fn, 0.02, 0.01, W, 0, 1, gather, state=bytes(part["state"]))
+    one = graph.estimate("5-clique", eps=0.02, delta=0.01, seed=seed, window=W)
+    assert one["rounds"] >= 2
+    for f in ("estimate", "ci_half_width", "eps_hat", "samples", "hits", "rounds", "converged", "sum", "sumsq"):
+        assert rest[f] == one[f], f
