@@ -68,14 +68,24 @@ _lock = threading.Lock()
 _lib = None
 
 
+# OG_SANITIZE=1 builds and loads a separate copy instrumented with gcc's
+# AddressSanitizer and UndefinedBehaviorSanitizer (errors abort the process;
+# run under LD_PRELOAD=$(gcc -print-file-name=libasan.so) ASAN_OPTIONS=detect_leaks=0)
+SANITIZE = os.environ.get("OG_SANITIZE") == "1"
+if SANITIZE:
+    LIB = LIB.replace("liboracle.so", "liboracle_san.so")
+
+
 def build(force=False):
     """Compile oracle.c into liboracle.so (gcc, no fast-math, no FMA contraction)."""
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
         return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
+    san = ["-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=all", "-fno-omit-frame-pointer"] \
+        if SANITIZE else []
     subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
-                           "-fno-fast-math", "-o", tmp, SRC, "-lm"])
+                           "-fno-fast-math"] + san + ["-o", tmp, SRC, "-lm"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -8,7 +8,7 @@ import ctypes as C
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libgpm.so")
+LIB_PATH = os.path.join(PKG, "libgpm_san.so" if os.environ.get("GPM_SANITIZE") == "1" else "libgpm.so")
 
 MAX_K = 12
 

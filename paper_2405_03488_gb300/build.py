@@ -16,10 +16,19 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgpm.so")
+# GPM_SANITIZE=1: a separate copy whose host code carries gcc's AddressSanitizer
+# and UndefinedBehaviorSanitizer (run under
+# LD_PRELOAD=$(gcc -print-file-name=libasan.so) ASAN_OPTIONS=detect_leaks=0)
+SANITIZE = os.environ.get("GPM_SANITIZE") == "1"
+SAN_FLAGS = ["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined",
+             "-Xcompiler", "-fno-sanitize-recover=all", "-Xcompiler", "-fno-omit-frame-pointer"]
+if SANITIZE:
+    OUT_DIR = os.path.join(PKG, "_build_san")
+    LIB = os.path.join(PKG, "libgpm_san.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-         "-I", os.path.join(ROOT, "include")]
+         "-I", os.path.join(ROOT, "include")] + (SAN_FLAGS if SANITIZE else [])
 
 
 def _sources():
@@ -60,7 +69,7 @@ def build(verbose=False, extra=()):
             and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs)):
         return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
+    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + (SAN_FLAGS if SANITIZE else [])
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
