@@ -48,6 +48,10 @@ def test_batch_equals_single_runs_and_oracle(rmat14):
     W = 1 << 14
     res = g.estimate_batch(pats, eps, delta=0.01, seed=5, window=W, n_max=1 << 22)
     assert len(res) == 21
+    again = g.estimate_batch(pats, eps, delta=0.01, seed=5, window=W, n_max=1 << 22)
+    for a, b in zip(res, again):      # run-to-run: the fixed chunk-order reduction is deterministic
+        for f in FIELDS:
+            assert a[f] == b[f], f
     for q, (pat, e) in enumerate(zip(pats, eps)):
         single = g.estimate(pat, eps=e, delta=0.01, seed=5, window=W, n_max=1 << 22, slot=q)
         for f in FIELDS:
