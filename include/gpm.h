@@ -347,6 +347,17 @@ gpm_status gpm_train_proposal(gpm_graph *g, const gpm_pattern *pattern, uint64_t
 gpm_status gpm_sparsify(gpm_graph *g, uint32_t colors, uint64_t seed, uint32_t colouring, uint32_t slot,
                         uint64_t *row_out, uint32_t *col_out, uint64_t *kept);
 
+/* The multi-GPU form of GS (Sec. 2.2.2, 5.2): the exact count, on the colour-
+ * sparsified graph of gpm_sparsify (colors, seed, colouring, slot), of the
+ * matches in the colour classes c with c mod world == rank.  A match of the
+ * sparsified graph lies inside one class, so the counts of ranks 0..world-1
+ * add up to its exact count (one integer all-reduce); times c^(k-1) that is
+ * GS's estimate.  max_seconds bounds the search as in gpm_estimate
+ * (GPM_ERR_NOT_CONVERGED with a lower bound).  rank < world. */
+gpm_status gpm_gs_count_classes(gpm_graph *g, const gpm_pattern *pattern, uint32_t colors, uint64_t seed,
+                                uint32_t colouring, uint32_t slot, uint32_t rank, uint32_t world, double max_seconds,
+                                uint64_t *count);
+
 /* Bernoulli edge sparsification (Algorithm 2): keep probability p realised as
  * t / 2^32 with t = floor(p * 2^32) (t = 2^32 for p >= 1); edge {u, w} stays
  * iff the first word of Philox4x32-10 at counter (min(u, w), max(u, w),

@@ -114,6 +114,7 @@ SIGNATURES = [
     ("gpm_train_proposal", _i32, [_V, P(Pattern), _u64, _u64, _u32, _u32, C.c_float, _V, _V, P(_dbl), P(_u64)]),
     ("gpm_sparsify", _i32, [_V, _u32, _u64, _u32, _u32, _V, _V, P(_u64)]),
     ("gpm_sparsify_edges", _i32, [_V, _dbl, _u64, _u32, _u32, _V, _V, P(_u64)]),
+    ("gpm_gs_count_classes", _i32, [_V, P(Pattern), _u32, _u64, _u32, _u32, _u32, _u32, _dbl, P(_u64)]),
     ("gpm_abort", _i32, [_V]),
     ("gpm_gather_probe", _i32, [_u64, _u32, _u64, P(_dbl)]),
     ("gpm_plan", _i32, [P(Pattern), P(_i32), P(_i32), P(_i32), P(_i32), P(_i32)]),

@@ -189,6 +189,15 @@ class Graph:
                                        C.c_void_p(col.data_ptr()), C.byref(kept)), "gpm_sparsify")
         return row, col[:kept.value]
 
+    def gs_count_classes(self, pat, colors, seed, rank, world, colouring=0, slot=0, max_seconds=0.0):
+        """Exact count, on the colour-sparsified graph, of the matches in the colour
+        classes c = rank (mod world): one rank's share of a sharded GS count."""
+        out = C.c_uint64()
+        pp = pattern(pat)
+        check(_lib.load().gpm_gs_count_classes(self.h, C.byref(pp), colors, seed, colouring, slot, rank, world,
+                                               max_seconds, C.byref(out)), "gpm_gs_count_classes")
+        return out.value
+
     def sparsify_edges(self, p, seed, colouring=0, slot=0):
         """Bernoulli edge sparsification (keep probability p) into new CUDA tensors (row_ptr, col)."""
         row = torch.empty(self.n + 1, dtype=torch.int64, device="cuda")

@@ -53,6 +53,15 @@ __global__ void colour_kernel(uint64_t n, uint32_t c, uint64_t seed, uint32_t co
     colours[v] = (uint32_t)(((uint64_t)o.x * (uint64_t)c) >> 32);
 }
 
+// Sharding by colour class: a vertex whose class c has c mod world != rank
+// gets a colour of its own (never below c, never another vertex's), so none
+// of its edges survives and only the rank's classes remain.
+__global__ void class_mask(uint64_t n, uint32_t rank, uint32_t world, uint32_t *colours) {
+    const uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    if (colours[v] % world != rank) colours[v] = 0xFFFFFFFFu - (uint32_t)v;
+}
+
 __global__ void keep_count(const uint64_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
                            const uint32_t *__restrict__ colours, uint64_t n, uint64_t *cnt) {
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -372,7 +381,7 @@ gpm_status exact_count_plan(gpm_graph *h, const Plan &p, uint64_t *out, float *k
 // Colour + sparsify into freshly allocated device arrays (caller frees).
 gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colouring, uint32_t slot,
                           uint64_t **row_out, uint32_t **col_out, uint64_t *kept, uint64_t *user_row,
-                          uint32_t *user_col, uint64_t bes_t) {
+                          uint32_t *user_col, uint64_t bes_t, uint32_t class_rank, uint32_t class_world) {
     const uint64_t n = h->d.n;
     cudaStream_t st = h->stream;
     uint32_t *colours = nullptr;
@@ -394,6 +403,7 @@ gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colo
         bes_count<<<blocks_w, 256, 0, st>>>(h->d.row_ptr, h->d.col, n, seed, colouring, slot, bes_t, cnt);
     } else if (n) {
         colour_kernel<<<blocks_v, 256, 0, st>>>(n, c, seed, colouring, slot, colours);
+        if (class_world > 1) class_mask<<<blocks_v, 256, 0, st>>>(n, class_rank, class_world, colours);
         keep_count<<<blocks_w, 256, 0, st>>>(h->d.row_ptr, h->d.col, colours, n, cnt);
     }
     e = cudaGetLastError();
@@ -524,6 +534,35 @@ extern "C" gpm_status gpm_exact_count(gpm_graph *h, const gpm_pattern *pattern, 
         return GPM_ERR_ARG;
     }
     return exact_count_plan(h, p, out, nullptr, 0.0);
+}
+
+extern "C" gpm_status gpm_gs_count_classes(gpm_graph *h, const gpm_pattern *pattern, uint32_t colors, uint64_t seed,
+                                           uint32_t colouring, uint32_t slot, uint32_t rank, uint32_t world,
+                                           double max_seconds, uint64_t *count) {
+    if (!h || !pattern || !count || colors == 0 || world == 0 || rank >= world || h->d.n >= 0xFFFFFFFFull - colors) {
+        set_error("gpm_gs_count_classes: null argument, zero colours or rank >= world");
+        return GPM_ERR_ARG;
+    }
+    Plan p;
+    std::string why = build_plan(*pattern, &p);
+    if (!why.empty()) {
+        set_error("pattern rejected: " + why);
+        return GPM_ERR_ARG;
+    }
+    uint64_t *row = nullptr;
+    uint32_t *col = nullptr;
+    uint64_t kept = 0;
+    gpm_status st = sparsify_alloc(h, colors, seed, colouring, slot, &row, &col, &kept, nullptr, nullptr, 0, rank, world);
+    if (st != GPM_OK) return st;
+    gpm_graph *gs = nullptr;
+    st = gpm_load_csr(h->d.n, row, col, GPM_DEVICE_PTRS, h->stream, &gs);
+    uint64_t cp = 0;
+    if (st == GPM_OK) st = exact_count_plan(gs, p, &cp, nullptr, max_seconds);
+    if (gs) gpm_free_graph(gs);
+    cudaFree(row);
+    cudaFree(col);
+    *count = cp;
+    return st;
 }
 
 extern "C" gpm_status gpm_sparsify_edges(gpm_graph *h, double p, uint64_t seed, uint32_t colouring, uint32_t slot,

@@ -130,7 +130,7 @@ gpm_status gs_estimate(gpm_graph *h, const Plan &p, uint64_t seed, double delta,
                        gpm_result *out);
 gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colouring, uint32_t slot,
                           uint64_t **row_out, uint32_t **col_out, uint64_t *kept, uint64_t *user_row,
-                          uint32_t *user_col, uint64_t bes_t = 0);
+                          uint32_t *user_col, uint64_t bes_t = 0, uint32_t class_rank = 0, uint32_t class_world = 1);
 double normal_quantile(double p);
 gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const double *eps, double delta,
                           uint64_t seed, const gpm_config *cfg, gpm_result *results, int mode);

@@ -100,3 +100,25 @@ def estimate_sharded(partials_fn, eps, delta, window, rank, world, gather, n_min
     return {"estimate": st.mu, "ci_half_width": st.half, "eps_hat": st.eps_hat, "samples": st.n,
             "hits": st.hits, "rounds": st.rounds, "converged": st.converged, "sum": st.sum, "sumsq": st.sumsq,
             "active": st.active, "state": st}
+
+
+def torch_allreduce_sum(group=None):
+    """Integer sum over torch.distributed ranks (gloo or NCCL)."""
+    import torch
+    import torch.distributed as dist
+
+    def allreduce(x):
+        dev = torch.device("cuda") if dist.get_backend(group) == "nccl" else torch.device("cpu")
+        t = torch.tensor([int(x)], dtype=torch.int64, device=dev)
+        dist.all_reduce(t, group=group)
+        return int(t.item())
+
+    return allreduce
+
+
+def gs_estimate_sharded(count_fn, colors, k, rank, world, allreduce):
+    """GS over ranks by colour class: count_fn(rank, world) is this rank's
+    exact count over its classes (``Graph.gs_count_classes``), allreduce sums
+    the integers; the estimate is the total times colors^(k-1)."""
+    total = allreduce(count_fn(rank, world))
+    return {"exact_count": total, "estimate": float(total) * float(colors) ** (k - 1)}

@@ -202,3 +202,24 @@ def test_gs_edge_mode_refuses_vertex_induced_patterns():
     k, edges = G.pattern("4-cycle")
     with pytest.raises(_lib.GpmError):
         g.estimate((k, edges, True), scheme=api.GS, edge_p=0.5)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3])
+def test_gs_counts_by_colour_class_add_up(world):
+    """The multi-GPU form of GS with the ranks run one after another: each
+    rank's class count equals the oracle's on the same classes, and the ranks
+    add up to the unsharded GS count."""
+    rp, col = G.erdos_renyi(3000, 0.02, seed=12)
+    g, og = pair(rp, col)
+    k, edges = G.pattern("4-clique")
+    whole = g.estimate("4-clique", scheme=api.GS, seed=31, colors=4)["exact_count"]
+    cols = O.colors(og.n, 4, 31).astype(np.uint64)
+    v = np.arange(og.n, dtype=np.uint64)
+    total = 0
+    for r in range(world):
+        cnt = g.gs_count_classes("4-clique", 4, 31, r, world)
+        masked = np.where(cols % world == r, cols, np.uint64(0xFFFFFFFF) - v).astype(np.uint32)
+        row, cc = O.sparsify(og, masked)
+        assert cnt == O.exact_count(O.Graph(row, cc), O.plan(k, edges))
+        total += cnt
+    assert total == whole > 0

@@ -189,3 +189,43 @@ def test_checkpoint_and_resume_equal_the_uninterrupted_run():
     rest = sharded.estimate_sharded(fn, EPS, DELTA, W, 0, 1, gather, state=saved)
     for f in ("estimate", "ci_half_width", "eps_hat", "samples", "hits", "rounds", "converged", "sum", "sumsq"):
         assert rest[f] == full[f], f
+
+
+def masked_colours(n, c, seed, rank, world):
+    """Colours with every class c != rank (mod world) replaced by one colour per
+    vertex, so only the rank's classes keep edges."""
+    cols = O.colors(n, c, seed).astype(np.uint64)
+    v = np.arange(n, dtype=np.uint64)
+    return np.where(cols % world == rank, cols, np.uint64(0xFFFFFFFF) - v).astype(np.uint32)
+
+
+def _gs_rank_main(rank, world, port, rp, col, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    torch.distributed.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        og = O.Graph(rp, col)
+        k, edges = G.pattern("4-clique")
+        p = O.plan(k, edges)
+
+        def count_fn(r, w):
+            row, cc = O.sparsify(og, masked_colours(og.n, 4, 23, r, w))
+            return O.exact_count(O.Graph(row, cc), p)
+
+        res = sharded.gs_estimate_sharded(count_fn, 4, k, rank, world, sharded.torch_allreduce_sum())
+        np.save(os.path.join(out_dir, "g%d.npy" % rank), np.array([res["exact_count"], res["estimate"]]))
+    finally:
+        torch.distributed.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_gs_by_colour_class(tmp_path):
+    """Sharded GS: each rank counts the matches of its colour classes; the
+    integer all-reduce equals the count on the whole sparsified graph."""
+    rp, col = G.to_numpy(*G.erdos_renyi(400, 0.12, seed=9))
+    mp.spawn(_gs_rank_main, args=(2, free_port(), rp, col, str(tmp_path)), nprocs=2, join=True)
+    g0, g1 = (np.load(os.path.join(tmp_path, "g%d.npy" % r)) for r in (0, 1))
+    assert np.array_equal(g0, g1)
+    og = O.Graph(rp, col)
+    k, edges = G.pattern("4-clique")
+    est, cp = O.gs_estimate(og, O.plan(k, edges), 4, seed=23)
+    assert cp > 0 and g0[0] == cp and g0[1] == est
