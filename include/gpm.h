@@ -121,10 +121,12 @@ typedef struct {
 
 typedef struct {
     double estimate;        /* mu, the estimated count */
-    double ci_half_width;   /* z * sigma (Algorithm 3), z = Phi^-1(1 - delta/2) */
-    double eps_hat;         /* predicted relative error z * sigma / mu (Eq. equ:error) */
+    double ci_half_width;   /* z * sigma (Algorithm 3), z = Phi^-1(1 - delta/2); GS: z s / sqrt(R)
+                               over R >= 2 samplers, NaN for one */
+    double eps_hat;         /* predicted relative error z * sigma / mu (Eq. equ:error); GS: the
+                               interval over the estimate, NaN for one sampler */
     double sum, sumsq;      /* running sum X_i and sum X_i^2 over all samples */
-    uint64_t samples;       /* n at the stop, a multiple of the window */
+    uint64_t samples;       /* n at the stop, a multiple of the window; GS: the samplers R */
     uint64_t hits;          /* samples with every candidate set non-empty */
     uint64_t rounds;        /* convergence rounds run */
     int32_t scheme_used;    /* gpm_scheme that produced the estimate */
@@ -133,7 +135,8 @@ typedef struct {
     double t_pilot_s;       /* hybrid: pilot NS round and cost models */
     double t_preproc_s;     /* GS: colouring and sparsification */
     double t_sample_s;      /* device time of the sampling / counting kernels (CUDA events) */
-    uint64_t exact_count;   /* GS: count on the sparsified graph; EXACT: the count */
+    uint64_t exact_count;   /* GS: count on the sparsified graph(s), summed over the samplers;
+                               EXACT: the count */
     uint64_t kernel_launches; /* kernels this call launched */
 } gpm_result;
 
