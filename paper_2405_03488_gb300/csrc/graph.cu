@@ -51,7 +51,12 @@ cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st) {
 }
 
 void pool_free(void *p, cudaStream_t st) {
-    if (p) cudaFreeAsync(p, st);
+    if (!p) return;
+    // a stream the caller has destroyed cannot order the free: free synchronously
+    if (cudaFreeAsync(p, st) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p);
+    }
 }
 
 thread_local std::string g_last_error;
