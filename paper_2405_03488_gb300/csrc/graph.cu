@@ -278,6 +278,7 @@ extern "C" gpm_status gpm_load_csr(uint64_t n, const uint64_t *row_ptr, const ui
     gpm_graph *g = new (std::nothrow) gpm_graph;
     if (!g) return GPM_ERR_OOM;
     std::memset(g, 0, sizeof(*g));
+    g->totals_host = g->totals_buf;
     g->stream = (cudaStream_t)stream;
     cudaStream_t st = g->stream;
     auto fail = [&](gpm_status s) {
@@ -323,8 +324,7 @@ extern "C" gpm_status gpm_load_csr(uint64_t n, const uint64_t *row_ptr, const ui
     if (pool_alloc((void **)&g->up, sizeof(uint64_t) * (n + 1), st) != cudaSuccess ||
         pool_alloc((void **)&g->uoff, sizeof(uint64_t) * (n + 1), st) != cudaSuccess ||
         pool_alloc((void **)&g->totals, sizeof(Totals) * 2, st) != cudaSuccess ||
-        pool_alloc((void **)&g->counter, sizeof(unsigned int) * 64, st) != cudaSuccess ||
-        cudaMallocHost((void **)&g->totals_host, sizeof(Totals) * 2) != cudaSuccess) {
+        pool_alloc((void **)&g->counter, sizeof(unsigned int) * 64, st) != cudaSuccess) {
         set_error("gpm_load_csr: device allocation failed");
         return fail(GPM_ERR_OOM);
     }
@@ -418,7 +418,7 @@ extern "C" void gpm_free_graph(gpm_graph *g) {
     pool_free(g->partials, g->stream);
     pool_free(g->totals, g->stream);
     pool_free(g->counter, g->stream);
-    if (g->totals_host) cudaFreeHost(g->totals_host);
+    g->totals_host = nullptr;
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     delete g;

@@ -150,7 +150,8 @@ struct gpm_graph {
     gpm::Partial *partials;
     uint64_t partials_cap;
     gpm::Totals *totals;          // device
-    gpm::Totals *totals_host;     // pinned
+    gpm::Totals *totals_host;     // points at totals_buf (each copy into it is followed by a stream sync)
+    gpm::Totals totals_buf[2];
     unsigned int *counter;        // device chunk counter
     volatile int abort_flag;
     int sm_count;
