@@ -236,7 +236,9 @@ def random_mlp(seed):
 
 TREE_CASES = [("triangle", False), ("4-clique", False), ("4-cycle", False), ("4-cycle", True),
               ("diamond", False), ("tailed-triangle", True), ("3-star", False), ("4-path", True),
-              ("house", False), ("5-clique", False)]
+              ("house", False), ("5-clique", False),
+              # edge-induced patterns with single-back-neighbour steps
+              ("wedge", False), ("4-path", False), ("5-path", False), ("dumbbell", False)]
 
 
 @pytest.mark.parametrize("name,induced", TREE_CASES)
