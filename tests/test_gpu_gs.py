@@ -223,3 +223,17 @@ def test_gs_counts_by_colour_class_add_up(world):
         assert cnt == O.exact_count(O.Graph(row, cc), O.plan(k, edges))
         total += cnt
     assert total == whole > 0
+
+
+@pytest.mark.parametrize("name,eps", [("4-clique", 0.005), ("triangle", 0.005), ("4-cycle", 0.002)])
+def test_pilot_sample_count_predicts_the_online_run(name, eps):
+    """The hybrid's NS cost rests on N_s = (z sd / (eps mu))^2 from a pilot
+    round (Sec. 4.3 with Eq. equ:error): the online run to the same target
+    needs about that many samples (within window rounding and the pilot's
+    sampling error)."""
+    rp, col = G.rmat(14, 16, seed=3)
+    g = api.Graph(rp.cuda(), col.cuda())
+    info = g.hybrid_model(name, eps=eps, delta=0.01, seed=3, window=1 << 16)
+    r = g.estimate(name, eps=eps, delta=0.01, seed=3, window=1 << 14, n_max=1 << 32)
+    assert r["converged"] == 1 and info["n_s"] > 8 * (1 << 14)
+    assert 0.5 < r["samples"] / info["n_s"] < 2.0, (r["samples"], info["n_s"])
