@@ -276,23 +276,26 @@ gpm_status gpm_merge_partials(const gpm_partial *parts, uint64_t n, gpm_sums *ou
 gpm_status gpm_window_update(gpm_window *w, const gpm_sums *window, double z, double eps, uint64_t n_min,
                              uint64_t n_max);
 
-/* Same result as gpm_sample_sums, for callers that must not allocate device
- * memory during the call.  The paper has no counterpart: this is a library
- * convenience.  It is meant for code that records work into a CUDA graph by
- * stream capture (where the implicit device synchronisation of cudaMalloc is
- * not allowed), for applications whose own memory pool has already reserved
- * the device memory, and for latency-bound loops that cannot afford an
- * allocation's synchronisation.  Instead of handle-owned buffers it keeps its
- * scratch (per-chunk partials, chunk counter, totals) in one fixed array of
- * about 2 MiB that every GPU loading the library holds until the process
- * exits.  Limits and rules:
- *  - count <= 2^26 samples per call, else GPM_ERR_ARG (nothing launched);
+/* Same totals as gpm_sample_sums, bit for bit, for callers that cannot
+ * allocate device memory while they run: applications that reserve all their
+ * device memory up front in a pool of their own (so a cudaMalloc would fail or
+ * fragment that pool), and latency-bound loops that cannot afford the device
+ * synchronisation an allocation implies.  The paper has no counterpart: this
+ * is a library convenience.  Instead of handle-owned buffers the call keeps
+ * its scratch (per-chunk partials, chunk counter, totals) in one fixed array
+ * of about 2 MiB that every GPU loading the library holds until the process
+ * exits.  It still synchronises the handle's stream to read the totals back.
+ * Limits and rules:
+ *  - count <= 2^22 samples per call (65,536 chunks of the fixed 64 samples),
+ *    else GPM_ERR_ARG with nothing launched; split larger ranges into calls
+ *    and add their totals;
  *  - the handle must come from gpm_load_csr (which allocates once, up front);
- *  - the first call on a device looks up the array's device address, so make
- *    that first call before any stream capture begins;
+ *  - the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current;
  *  - all calls in the process share the one array and leave their contents in
- *    it: calls whose work overlaps on the GPU (other streams, other threads)
- *    race and must be serialised by the caller. */
+ *    it (each call resets the chunk counter it needs): calls whose work
+ *    overlaps on the GPU (other streams, other threads) race and must be
+ *    serialised by the caller. */
 gpm_status gpm_sample_sums_static(gpm_graph *g, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
                                   uint64_t count, const gpm_config *cfg, gpm_sums *out);
 

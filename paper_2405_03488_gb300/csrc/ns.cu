@@ -174,6 +174,17 @@ static cudaError_t launch_ns(gpm_graph *h, const Plan &p, const Shape &sh, const
     return cudaGetLastError();
 }
 
+// The compiled sampler variant for a kernel mode (kernel_mode's result).
+template <bool TRACE>
+static cudaError_t launch_mode(gpm_graph *h, const Plan &p, const Shape &sh, const RunArgs &a, int kmode) {
+    switch (kmode) {
+        case MODE_CHECK: return launch_ns<MODE_CHECK, TRACE>(h, p, sh, a);
+        case MODE_LEARNED: return launch_ns<MODE_LEARNED, TRACE>(h, p, sh, a);
+        case MODE_INTERSECT_SINGLE: return launch_ns<MODE_INTERSECT_SINGLE, TRACE>(h, p, sh, a);
+        default: return launch_ns<MODE_INTERSECT, TRACE>(h, p, sh, a);
+    }
+}
+
 static gpm_status ensure_partials(gpm_graph *h, uint64_t n) {
     if (h->partials_cap >= n) return GPM_OK;
     pool_free(h->partials, h->stream);
@@ -227,16 +238,8 @@ static gpm_status run_block(gpm_graph *h, const Plan &p, int mode, uint64_t seed
         return GPM_ERR_CUDA;
     }
     if (kernel_ms) cudaEventRecord(h->ev0, h->stream);
-    cudaError_t e;
-    if (mode == MODE_CHECK)
-        e = trace ? launch_ns<MODE_CHECK, true>(h, p, sh, a) : launch_ns<MODE_CHECK, false>(h, p, sh, a);
-    else if (mode == MODE_LEARNED)
-        e = trace ? launch_ns<MODE_LEARNED, true>(h, p, sh, a) : launch_ns<MODE_LEARNED, false>(h, p, sh, a);
-    else if (kernel_mode(mode, plan_single_steps(p)) == MODE_INTERSECT_SINGLE)
-        e = trace ? launch_ns<MODE_INTERSECT_SINGLE, true>(h, p, sh, a)
-                  : launch_ns<MODE_INTERSECT_SINGLE, false>(h, p, sh, a);
-    else
-        e = trace ? launch_ns<MODE_INTERSECT, true>(h, p, sh, a) : launch_ns<MODE_INTERSECT, false>(h, p, sh, a);
+    const int kmode = kernel_mode(mode, plan_single_steps(p));
+    cudaError_t e = trace ? launch_mode<true>(h, p, sh, a, kmode) : launch_mode<false>(h, p, sh, a, kmode);
     if (kernel_ms) cudaEventRecord(h->ev1, h->stream);
     if (e != cudaSuccess) {
         set_error(std::string("sampler launch: ") + cudaGetErrorString(e));
@@ -744,10 +747,13 @@ extern "C" gpm_status gpm_estimate(gpm_graph *h, const gpm_pattern *pattern, gpm
 // gpm_sample_sums, with every scratch word (per-chunk partials, the chunk
 // counter, the totals) in one file-scope device array instead of memory the
 // handle allocates, so the call itself allocates no device or pinned memory.
+// The chunk size stays the fixed 64 samples of every other path, so the
+// array's 65,536 partials bound a call to 2^22 samples and the totals equal
+// gpm_sample_sums's bit for bit.
 namespace gpm {
 
-constexpr uint32_t kStaticMaxChunks = 1u << 16;          // partials per call
-constexpr uint64_t kStaticMaxSamples = 1ull << 26;       // samples per call
+constexpr uint32_t kStaticMaxChunks = 1u << 16;                          // partials per call
+constexpr uint64_t kStaticMaxSamples = (uint64_t)kStaticMaxChunks * kChunk;   // 2^22 samples per call
 constexpr size_t kStaticPartialBytes = sizeof(Partial) * kStaticMaxChunks;
 constexpr size_t kStaticScratchBytes = kStaticPartialBytes + 256 + 256;   // partials | totals | counter
 
@@ -790,7 +796,7 @@ extern "C" gpm_status gpm_sample_sums_static(gpm_graph *h, const gpm_pattern *pa
         return GPM_ERR_ARG;
     }
     if (count > kStaticMaxSamples) {
-        set_error("gpm_sample_sums_static: count exceeds the static scratch limit of 2^26 samples per call");
+        set_error("gpm_sample_sums_static: count exceeds the static scratch limit of 2^22 samples per call");
         return GPM_ERR_ARG;
     }
     Plan p;
@@ -809,9 +815,7 @@ extern "C" gpm_status gpm_sample_sums_static(gpm_graph *h, const gpm_pattern *pa
     const int mode = mode_of(cfg);
     if (sh.cap == 0) sh.cap = default_cap(h, 0, sh.warps, mode, p.induced);
     if (mode == MODE_LEARNED && sh.cap < kLearnedMax) sh.cap = kLearnedMax;
-    const uint64_t min_chunk = (count + kStaticMaxChunks - 1) / kStaticMaxChunks;
-    if (sh.chunk < min_chunk) sh.chunk = (uint32_t)min_chunk;
-    const uint64_t nchunks = (count + sh.chunk - 1) / sh.chunk;
+    const uint64_t nchunks = (count + sh.chunk - 1) / sh.chunk;   // <= kStaticMaxChunks
     RunArgs a;
     a.seed = seed;
     a.first = first;
@@ -828,10 +832,7 @@ extern "C" gpm_status gpm_sample_sums_static(gpm_graph *h, const gpm_pattern *pa
     if (mode == MODE_LEARNED) a.mlp = *cfg->mlp;
     cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess)
-        e = (mode == MODE_CHECK)     ? launch_ns<MODE_CHECK, false>(h, p, sh, a)
-            : (mode == MODE_LEARNED) ? launch_ns<MODE_LEARNED, false>(h, p, sh, a)
-            : plan_single_steps(p)   ? launch_ns<MODE_INTERSECT_SINGLE, false>(h, p, sh, a)
-                                     : launch_ns<MODE_INTERSECT, false>(h, p, sh, a);
+        e = launch_mode<false>(h, p, sh, a, kernel_mode(mode, plan_single_steps(p)));
     if (e == cudaSuccess) {
         reduce_partials<<<1, 1024, 0, h->stream>>>(parts, (uint32_t)nchunks, tot, 0);
         e = cudaGetLastError();
