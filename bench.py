@@ -1,21 +1,26 @@
 """Benchmark: time-to-converge at +-1% with 99% confidence, and samples/s, of
-neighbour sampling with eager verify on R-MAT scale 22 (edge factor 16),
-4-clique and 5-clique, through libgpm's C ABI on one GB300.
+neighbour sampling with eager verify, learned proposal + NS/GS selector head
+against plain NS, through libgpm's C ABI on one GB300.
 
+Headline workload (the default): R-MAT scale 27, edge factor 16 (134M
+vertices, about 2.1G undirected edges, a 17 GB u32 CSR), 5-clique and 4-cycle.
 A step estimates both patterns to eps = 1%, delta = 1% in one batched call
 (Algorithm 3 rounds of 2^20 samples per pattern, one persistent sampler launch
 per round, convergence checked on the device, rounds replayed as a CUDA
 graph), seed = step index.  ``value`` = samples/s over the timed steps with
 the graph resident in HBM; ``e2e`` repeats the steps through the public API
 from pinned host arrays (graph upload and result read-back inside the timed
-region).  After the timed steps the learned proposal is trained per pattern
-on plain-NS traces and both variants are run to the same target on the same
-seeds; that comparison is reported in ``learned_vs_plain``.
+region).  After the timed steps, per pattern, the learned proposal is trained
+on plain-NS traces and run to the same target, and the hybrid with the NS/GS
+selector head (trained on timed small-graph cases) runs too; that comparison
+is reported in ``learned_vs_plain``.
 
+--config rmat22 runs the same line on R-MAT scale 22 (4-clique + 5-clique);
+the other --config values print one JSON line per companion workload.
 --impl reference times the CPU oracle (the reference arm of this project) on
 the host cores over a bounded sample of the same workload.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--config NAME]
 """
 import argparse
 import json
@@ -29,13 +34,20 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-PATTERNS = ("4-clique", "5-clique")
 EPS, DELTA = 0.01, 0.01
-N_MAX = 1_000_000_000
 WINDOW = 1 << 20
-SCALE, EDGE_FACTOR, GRAPH_SEED = 22, 16, 2
 METRIC = "time-to-converge (+-1% @99% conf) and samples/s, learned vs plain NS"
-WORKLOAD = "R-MAT scale 22, edge factor 16 (a,b,c = 0.57,0.19,0.19), 4-clique + 5-clique NS eager-verify"
+
+# the line's workloads: R-MAT (a, b, c) = (0.57, 0.19, 0.19), edge factor 16
+WORKLOADS = {
+    "rmat27": {"scale": 27, "seed": 5, "patterns": ("5-clique", "4-cycle"), "n_max": 1 << 34,
+               "workload": "R-MAT scale 27, edge factor 16 (a,b,c = 0.57,0.19,0.19; 134M vertices, 2.1G edges), "
+                           "5-clique + 4-cycle NS eager-verify"},
+    "rmat22": {"scale": 22, "seed": 2, "patterns": ("4-clique", "5-clique"), "n_max": 1_000_000_000,
+               "workload": "R-MAT scale 22, edge factor 16 (a,b,c = 0.57,0.19,0.19), 4-clique + 5-clique NS "
+                           "eager-verify"},
+}
+COMPANIONS = ["er-triangle", "rmat24-batch", "chunglu-needle", "selector", "complex", "gs-variants"]
 
 
 def parse():
@@ -45,15 +57,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpm", choices=["gpm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--config", default="rmat22",
-                    choices=["rmat22", "er-triangle", "rmat24-batch", "chunglu-needle", "rmat27", "selector",
-                             "complex", "gs-variants"],
-                    help="workload; the default is the headline R-MAT 22 run, the others print one "
-                         "JSON line each for the companion workloads")
-    ap.add_argument("--ncu-case", default=None, choices=["4-clique", "5-clique"],
-                    help="profiling case: R-MAT 22 resident, --steps sampler launches of one window each")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned/selector-vs-plain comparison")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--config", default="rmat27", choices=list(WORKLOADS) + COMPANIONS,
+                    help="workload; rmat27 (default) and rmat22 print the bench line, the others one JSON line "
+                         "each for the companion workloads")
+    ap.add_argument("--ncu-case", default=None, choices=["4-clique", "5-clique", "4-cycle"],
+                    help="profiling case: the --config R-MAT graph resident, --warmup + --steps one-round "
+                         "estimates (one sampler launch of one window each)")
     return ap.parse_args()
 
 
@@ -66,6 +77,8 @@ def dist_env():
 
 # ------------------------------------------------------------------ clocks
 class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons; started before
+    the warm-up steps so that its start-up does not fall in the timed region."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -74,8 +87,9 @@ class Clocks:
         self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
         self.idx = gpu_index
         self.proc = None
+        self.t_mark = None
 
-    def start(self):
+    def start(self, wait_s=10.0):
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
@@ -83,6 +97,19 @@ class Clocks:
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # wait for the first sample: the tool is up and polling
+        t0 = time.time()
+        while time.time() - t0 < wait_s and self.proc.poll() is None:
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
+
+    def mark(self):
+        """Start of the timed region: samples before it are dropped."""
+        self.t_mark = time.time()
+        self._lines_before = sum(1 for _ in open(self.path)) if self.proc else 0
 
     def stop(self):
         if self.proc is None:
@@ -93,7 +120,9 @@ class Clocks:
         self.f.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        lines = open(self.path).read().splitlines()
+        lines = lines[getattr(self, "_lines_before", 0):] or lines[-1:]
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -114,9 +143,9 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ workload
-def make_graph(device):
+def make_graph(wl, device):
     from paper_2405_03488_gb300 import graphs as G
-    return G.rmat(SCALE, EDGE_FACTOR, seed=GRAPH_SEED, device=device)
+    return G.rmat(wl["scale"], 16, seed=wl["seed"], device=device)
 
 
 def measured_peaks():
@@ -138,10 +167,11 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def ncu_traffic():
-    """Per-launch DRAM traffic of the sampler from the committed ncu summary,
-    if it was taken on the current kernel sources."""
-    summ = os.path.join(ROOT, "profiles", "ns_batch_kernel_rmat22.md")
+def ncu_traffic(config):
+    """Per-launch DRAM traffic of the sampler, scaled to one full launch of this
+    workload, from the committed ncu summary, if it was taken on the current
+    kernel sources."""
+    summ = os.path.join(ROOT, "profiles", "ns_batch_kernel_%s.md" % config)
     if not os.path.exists(summ):
         return None
     txt = open(summ).read()
@@ -153,58 +183,100 @@ def ncu_traffic():
 
 
 # ------------------------------------------------------------------ CPU oracle (cpu_baseline / reference arm)
-def _oracle_worker(args):
-    rp_path, col_path, name, seed, first, count = args
-    import numpy as np
-    sys.path.insert(0, ROOT)
+# The oracle is plain single-threaded C called through ctypes, which releases
+# the GIL, so a thread pool runs one oracle call per host core on one shared
+# view of the graph.
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_graph(rp_np, col_np):
+    from oracle import oracle as O
+    return O.Graph(rp_np, col_np)
+
+
+def oracle_sample(og, patterns, budget_s, seed=1):
+    """Runs the oracle as it stands over a bounded prefix of each pattern's
+    sample stream, split into per-core slices.  Returns per-pattern totals,
+    the wall time and the core count."""
+    import concurrent.futures as cf
     from oracle import oracle as O
     from paper_2405_03488_gb300 import graphs as G
-    rp = np.load(rp_path, mmap_mode="r")
-    col = np.load(col_path, mmap_mode="r")
-    g = O.Graph(rp, col)
-    k, edges = G.pattern(name)
-    p = O.plan(k, edges)
-    t0 = time.perf_counter()
-    acc, _ = O.ns_run(g, p, seed=seed, first=first, count=count, want_bytes=True)
-    dt = time.perf_counter() - t0
-    return name, acc.n, acc.hits, acc.sum, acc.sumsq, acc.bytes, dt
+    cores = host_cores()
+    plans = {name: O.plan(*G.pattern(name)) for name in patterns}
 
+    def work(job):
+        name, first, count = job
+        t0 = time.perf_counter()
+        acc, _ = O.ns_run(og, plans[name], seed=seed, first=first, count=count, want_bytes=True)
+        return name, acc.n, acc.hits, acc.sum, acc.sumsq, acc.bytes, time.perf_counter() - t0
 
-def oracle_sample(rp_np, col_np, budget_s, seed=1):
-    """Runs the oracle as it stands over a bounded prefix of each pattern's
-    sample stream, split across the host cores (spawned processes).  Returns
-    per-pattern totals and the wall time."""
-    import multiprocessing as mp
-    import numpy as np
-    tmp = tempfile.mkdtemp(prefix="gpm_oracle_")
-    rp_path, col_path = os.path.join(tmp, "rp.npy"), os.path.join(tmp, "col.npy")
-    np.save(rp_path, rp_np)
-    np.save(col_path, col_np)
-    cores = os.cpu_count() or 1
-    ctx = mp.get_context("spawn")
-    out = {}
-    with ctx.Pool(cores) as pool:
-        # calibrate: a short single-process run per pattern
+    with cf.ThreadPoolExecutor(cores) as pool:
+        # calibrate each pattern on one core
         rate = {}
-        for name in PATTERNS:
-            r = pool.apply(_oracle_worker, ((rp_path, col_path, name, seed, 0, 4000),))
+        for name in patterns:
+            n0 = 2000
+            while True:
+                r = pool.submit(work, (name, 0, n0)).result()
+                if r[6] > 0.2 or n0 >= 1 << 22:
+                    break
+                n0 *= 4
             rate[name] = r[1] / max(r[6], 1e-6)
         t0 = time.perf_counter()
         jobs = []
-        for name in PATTERNS:
-            per_core = max(1000, int(rate[name] * budget_s / len(PATTERNS)))
-            for c in range(cores):
-                jobs.append((rp_path, col_path, name, seed, c * per_core, per_core))
-        res = pool.map(_oracle_worker, jobs)
+        for name in patterns:
+            per_core = max(256, int(rate[name] * budget_s / len(patterns)))
+            jobs += [(name, c * per_core, per_core) for c in range(cores)]
+        res = list(pool.map(work, jobs))
         wall = time.perf_counter() - t0
-    for name in PATTERNS:
+    out = {}
+    for name in patterns:
         rows = [r for r in res if r[0] == name]
         out[name] = {"n": sum(r[1] for r in rows), "hits": sum(r[2] for r in rows),
                      "sum": sum(r[3] for r in rows), "bytes": sum(r[5] for r in rows)}
-    for pth in (rp_path, col_path):
-        os.unlink(pth)
-    os.rmdir(tmp)
     return out, wall, cores
+
+
+def oracle_online_parallel(og, name, eps, delta, seed, window, n_max, time_cap, induced=False):
+    """Algorithm 3 with the oracle on every host core: each window of W samples
+    is split into per-core slices of consecutive indices, the slices' sums are
+    added in slice order, and the window test stops the run (the oracle's own
+    error formula and Phi^-1).  Returns (time, samples, estimate, eps_hat,
+    converged)."""
+    import concurrent.futures as cf
+    from oracle import oracle as O
+    from paper_2405_03488_gb300 import graphs as G
+    k, edges = G.pattern(name)
+    p = O.plan(k, edges, induced=induced)
+    cores = host_cores()
+    z = O.phi_inv(1.0 - delta / 2.0)
+    per = (window + cores - 1) // cores
+    n, s1, s2 = 0, 0.0, 0.0
+    t0 = time.perf_counter()
+    mu = eh = float("nan")
+    converged = False
+    with cf.ThreadPoolExecutor(cores) as pool:
+        r = 0
+        while True:
+            base = r * window
+            jobs = [(base + c * per, min(per, window - c * per)) for c in range(cores) if c * per < window]
+            parts = list(pool.map(lambda j: O.ns_run(og, p, seed=seed, first=j[0], count=j[1])[0], jobs))
+            for a in parts:
+                s1 += a.sum
+                s2 += a.sumsq
+                n += a.n
+            mu, half, eh = O.error_of(s1, s2, n, z)
+            r += 1
+            if mu > 0 and eh <= eps:
+                converged = True
+                break
+            if n >= n_max or time.perf_counter() - t0 > time_cap:
+                break
+    return {"seconds": time.perf_counter() - t0, "samples": n, "estimate": mu, "eps_hat": eh,
+            "converged": converged, "cores": cores}
 
 
 def run_reference(args):
@@ -214,17 +286,21 @@ def run_reference(args):
         return
     import torch
     from paper_2405_03488_gb300 import graphs as G
+    wl = WORKLOADS.get(args.config, WORKLOADS["rmat27"])
     # the same realisation as the GPU arm (generated on the device when present)
-    rp, col = make_graph("cuda" if torch.cuda.is_available() else "cpu")
+    rp, col = make_graph(wl, "cuda" if torch.cuda.is_available() else "cpu")
     rp_np, col_np = G.to_numpy(rp, col)
     del rp, col
+    if torch.cuda.is_available():
+        torch.cuda.empty_cache()
+    og = oracle_graph(rp_np, col_np)
     budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        oracle_sample(rp_np, col_np, min(budget, 2.0))
+        oracle_sample(og, wl["patterns"], min(budget, 1.0))
     tot_n, tot_t = 0, 0.0
     cores = 1
     for step in range(args.steps):
-        res, wall, cores = oracle_sample(rp_np, col_np, budget, seed=step + 1)
+        res, wall, cores = oracle_sample(og, wl["patterns"], budget, seed=step + 1)
         tot_n += sum(v["n"] for v in res.values())
         tot_t += wall
     value = tot_n / tot_t
@@ -232,45 +308,16 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "patterns": list(PATTERNS), "eps": EPS, "delta": DELTA,
-                       "window": WINDOW, "l2": "inputs larger than L2 (0.5 GB CSR)"},
+            "config": {"workload": wl["workload"], "patterns": list(wl["patterns"]), "eps": EPS, "delta": DELTA,
+                       "window": WINDOW, "l2": "inputs larger than L2"},
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
-                             "sample": "per step about %.0f s of oracle work: a prefix of each pattern's "
-                                       "sample stream split over %d spawned processes" % (budget, cores)},
+                             "sample": "per step about %.1f s of oracle work: a prefix of each pattern's "
+                                       "sample stream split over %d threads" % (budget, cores)},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-# ------------------------------------------------------------------ learned vs plain
-def learned_vs_plain(g, api, seed=5):
-    """Per pattern: train the proposal on plain-NS traces (2^20 samples, 3
-    epochs of Adam), then run plain and learned NS to +-1% @ 99% on the same
-    seed, and measure hit rate and per-sample CV^2 on 2^20 further samples."""
-    import torch
-    out = {}
-    for name in PATTERNS:
-        prop = api.Proposal(seed=1)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        loss, rows = prop.train(g, name, seed=11, samples=1 << 20, epochs=3, batch=8192, lr=3e-3)
-        torch.cuda.synchronize()
-        train_s = time.perf_counter() - t0
-        row = {"train_s": train_s, "train_rows": rows, "train_loss": loss}
-        for variant in ("plain", "learned"):
-            kw = {"mlp": prop} if variant == "learned" else {}
-            sch = api.NS_LEARNED if variant == "learned" else api.NS
-            r = g.estimate(name, scheme=sch, eps=EPS, delta=DELTA, seed=seed, window=WINDOW, n_max=N_MAX, **kw)
-            s = g.sample_sums(name, seed=seed + 1, first=0, count=WINDOW, **kw)
-            mu = s.sum / s.n
-            row[variant] = {"time_to_converge_s": r["t_total_s"], "samples": r["samples"],
-                            "samples_per_s": r["samples"] / max(r["t_sample_s"], 1e-12),
-                            "estimate": r["estimate"], "eps_hat": r["eps_hat"], "hit_rate": s.hits / s.n,
-                            "cv2": (s.sumsq / s.n - mu * mu) / (mu * mu) if mu > 0 else None}
-        out[name] = row
-    return out
-
-
-# ------------------------------------------------------------------ companion workloads
+# ------------------------------------------------------------------ learned / selector vs plain
 def _timed(fn):
     import torch
     torch.cuda.synchronize()
@@ -280,174 +327,49 @@ def _timed(fn):
     return r, time.perf_counter() - t0
 
 
-def companion(args):
-    """One JSON line per companion workload (1 GPU)."""
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2405_03488_gb300 import api
-    from paper_2405_03488_gb300 import graphs as G
-    out = {"config": args.config}
-    if args.config == "er-triangle":
-        # G(n = 10^4, p = 0.002), triangle, 10^6 samples with seed 1; exact count for comparison
-        rp, col = G.erdos_renyi(10_000, 0.002, seed=1, device="cuda")
-        g = api.Graph(rp, col)
-        exact = g.exact_count("triangle")
-        for _ in range(args.warmup):
-            g.sample_sums("triangle", seed=1, first=0, count=10 ** 6)
-        s, t = _timed(lambda: g.sample_sums("triangle", seed=1, first=0, count=10 ** 6))
-        mu = s.sum / s.n
-        sd = ((s.sumsq / s.n - mu * mu) / s.n) ** 0.5
-        out.update({"n": g.n, "m": g.m, "samples": s.n, "seconds": t, "samples_per_s": s.n / t,
-                    "estimate": mu, "exact": exact, "rel_err": abs(mu - exact) / exact, "z": (mu - exact) / sd,
-                    "hit_rate": s.hits / s.n, "eps_hat_99": 2.5758293035489004 * sd / mu})
-        # empirical coverage of the convergence test: seeds 1..1000 at +-5% / 95% and +-1% / 99%
-        cov = {}
-        for eps, delta, R in ((0.05, 0.05, 1000), (0.01, 0.01, 1000)):
-            miss, samples, tt = 0, 0, 0.0
-            for sd_ in range(1, R + 1):
-                r, ts = _timed(lambda: g.estimate("triangle", eps=eps, delta=delta, seed=sd_, window=1 << 16))
-                miss += abs(r["estimate"] - exact) > eps * exact
-                samples += r["samples"]
-                tt += ts
-            cov["eps%g_delta%g" % (eps, delta)] = {"runs": R, "within_eps": 1 - miss / R, "nominal": 1 - delta,
-                                                   "mean_samples": samples / R, "mean_time_to_converge_s": tt / R}
-        out["coverage"] = cov
-    elif args.config == "rmat24-batch":
-        # one batched run: 6 connected 4-vertex motifs (vertex-induced) and triangles, eps 0.5/1/2 %
-        rp, col = G.rmat(24, 16, seed=3, device="cuda")
-        torch.cuda.synchronize()
-        torch.cuda.empty_cache()
-        g = api.Graph(rp, col)
-        pats, eps, names = [], [], []
-        for e in (0.005, 0.01, 0.02):
-            for nm in G.MOTIFS4 + ["triangle"]:
-                k, edges = G.pattern(nm)
-                pats.append((k, edges, nm != "triangle"))
-                eps.append(e)
-                names.append("%s@%g" % (nm, e))
-        best, tt = _timed(lambda: g.autotune(pats, seed=7, window=1 << 18))
-        for _ in range(args.warmup):
-            g.estimate_batch(pats, eps, seed=100, window=WINDOW, n_max=1 << 32, **best)
-        res, t = _timed(lambda: g.estimate_batch(pats, eps, seed=1, window=WINDOW, n_max=1 << 32, **best))
-        samples = sum(r["samples"] for r in res)
-        out.update({"n": g.n, "m": g.m, "jobs": len(pats), "autotuned": best, "autotune_s": tt,
-                    "time_to_converge_s": t, "samples": samples, "samples_per_s": samples / t,
-                    "kernel_s": res[0]["t_sample_s"], "rounds": max(r["rounds"] for r in res),
-                    "all_converged": all(r["converged"] for r in res),
-                    "per_job": {nm: {"estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"]}
-                                for nm, r in zip(names, res)}})
-    elif args.config == "chunglu-needle":
-        # Chung-Lu, 8M vertices, exponent 2.1, mean degree 20, 200 planted 12-cliques
-        rp, col = G.chung_lu(8_000_000, gamma=2.1, mean_degree=20.0, n_cliques=200, clique_size=12, seed=4,
-                             device="cuda")
-        torch.cuda.synchronize()
-        torch.cuda.empty_cache()
-        g = api.Graph(rp, col)
-        out.update({"n": g.n, "m": g.m, "max_degree": g.max_degree})
-        for name in ("7-clique", "8-clique"):
-            row = {}
-            r, te = _timed(lambda: g.estimate(name, scheme=api.EXACT, max_seconds=120.0))
-            exact = r["exact_count"]
-            row["exact"] = {"count": exact, "seconds": te, "complete": bool(r["converged"])}
-            r, t = _timed(lambda: g.estimate(name, eps=EPS, delta=DELTA, seed=1, window=WINDOW, n_max=1 << 32,
-                                             max_seconds=60.0))
-            row["ns"] = {"seconds": t, "estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"],
-                         "converged": r["converged"], "rel_err": abs(r["estimate"] - exact) / max(exact, 1)}
-            r, t = _timed(lambda: g.estimate(name, scheme=api.GS, seed=1, colors=8))
-            row["gs_c8"] = {"seconds": t, "estimate": r["estimate"], "sparsified_count": r["exact_count"],
-                            "rel_err": abs(r["estimate"] - exact) / max(exact, 1), "preproc_s": r["t_preproc_s"]}
-            r, t = _timed(lambda: g.estimate(name, scheme=api.HYBRID, eps=EPS, delta=DELTA, seed=1, window=WINDOW,
-                                             n_max=1 << 32, max_seconds=60.0, colors=8))
-            row["hybrid"] = {"seconds": t, "scheme": {0: "NS", 1: "GS"}.get(r["scheme_used"], r["scheme_used"]),
-                             "estimate": r["estimate"], "pilot_s": r["t_pilot_s"],
-                             "rel_err": abs(r["estimate"] - exact) / max(exact, 1)}
-            prop = api.Proposal(seed=1)
-            (loss, rows), ttrain = _timed(lambda: prop.train(g, name, seed=11, samples=1 << 21, epochs=3,
-                                                             batch=8192, lr=3e-3))
-            r, t = _timed(lambda: g.estimate(name, scheme=api.NS_LEARNED, eps=EPS, delta=DELTA, seed=1,
-                                             window=WINDOW, n_max=1 << 32, max_seconds=60.0, mlp=prop))
-            row["learned"] = {"seconds": t, "train_s": ttrain, "train_rows": rows, "estimate": r["estimate"],
-                              "eps_hat": r["eps_hat"], "samples": r["samples"], "converged": r["converged"],
-                              "rel_err": abs(r["estimate"] - exact) / max(exact, 1)}
-            for variant, kw in (("plain", {}), ("learned", {"mlp": prop})):
-                sm = g.sample_sums(name, seed=9, first=0, count=1 << 22, **kw)
-                mu = sm.sum / sm.n
-                row[variant + "_cv2"] = (sm.sumsq / sm.n - mu * mu) / (mu * mu) if mu > 0 else None
-                row[variant + "_hit_rate"] = sm.hits / sm.n
-            out[name] = row
-    elif args.config == "rmat27":
-        # the NS/GS selector head, trained on the timed small-graph cases first
-        (rows_s, labels_s, _, handles), t_cases = _timed(lambda: timed_selector_cases(api, G))
-        (sel, sel_loss), t_train = _timed(lambda: train_selector(api, rows_s, labels_s, next(iter(handles.values()))))
-        out["selector"] = {"cases": len(rows_s), "gs_faster": int(sum(labels_s)), "cases_s": t_cases,
-                           "train_s": t_train, "train_loss": sel_loss}
-        for h_ in handles.values():
-            h_.close()
-        del handles
-        torch.cuda.empty_cache()
-        # R-MAT scale 27, edge factor 16: about 2.1 billion undirected edges
-        rp, col = G.rmat(27, 16, seed=5, device="cuda")
-        torch.cuda.synchronize()
-        torch.cuda.empty_cache()
-        g, tl = _timed(lambda: api.Graph(rp, col))
-        out.update({"n": g.n, "m": g.m, "load_s": tl, "gpu_mem_gb": torch.cuda.max_memory_allocated() / 1e9})
-        for name in ("5-clique", "4-cycle"):
-            r, t = _timed(lambda: g.estimate(name, eps=EPS, delta=DELTA, seed=1, window=WINDOW, n_max=1 << 34,
-                                             max_seconds=120.0))
-            row = {"ns": {"seconds": t, "estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"],
-                          "samples_per_s": r["samples"] / max(r["t_sample_s"], 1e-12), "converged": r["converged"]}}
-            for label, kw in (("hybrid_cost_model", {}), ("hybrid_selector", {"selector": sel})):
-                r, t = _timed(lambda: g.estimate(name, scheme=api.HYBRID, eps=EPS, delta=DELTA, seed=1, window=WINDOW,
-                                                 n_max=1 << 34, max_seconds=120.0, colors=8, **kw))
-                row[label] = {"seconds": t, "engine": "GS" if r["scheme_used"] == api.GS else "NS",
-                              "estimate": r["estimate"], "pilot_s": r["t_pilot_s"], "converged": r["converged"]}
-            if name.endswith("clique"):
-                prop = api.Proposal(seed=1)
-                (loss, rows), ttrain = _timed(lambda: prop.train(g, name, seed=11, samples=1 << 20, epochs=2,
-                                                                 batch=8192, lr=3e-3))
-                r, t = _timed(lambda: g.estimate(name, scheme=api.NS_LEARNED, eps=EPS, delta=DELTA, seed=1,
-                                                 window=WINDOW, n_max=1 << 34, max_seconds=120.0, mlp=prop))
-                row["learned"] = {"seconds": t, "train_s": ttrain, "estimate": r["estimate"], "eps_hat": r["eps_hat"],
-                                  "samples": r["samples"], "converged": r["converged"]}
-            out[name] = row
-    elif args.config == "selector":
-        out.update(selector_study(api, G))
-    elif args.config == "complex":
-        # the paper's non-clique patterns (edge-induced), NS to +-1% at 99% on R-MAT 22
-        rp, col = make_graph("cuda")
-        torch.cuda.synchronize()
-        g = api.Graph(rp, col)
-        out.update({"n": g.n, "m": g.m, "eps": EPS, "delta": DELTA})
-        for name in ("5-path", "house", "dumbbell"):
-            k, edges = G.pattern(name)
-            pat = (k, edges, False)
-            for w in range(args.warmup):
-                g.estimate(pat, eps=EPS, delta=DELTA, seed=100 + w, window=WINDOW, n_max=1 << 36, max_seconds=60.0)
-            r, t = _timed(lambda: g.estimate(pat, eps=EPS, delta=DELTA, seed=1, window=WINDOW, n_max=1 << 36,
-                                             max_seconds=60.0))
-            out[name] = {"seconds": t, "estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"],
-                         "hit_rate": r["hits"] / max(r["samples"], 1),
-                         "samples_per_s": r["samples"] / max(r["t_sample_s"], 1e-12), "converged": r["converged"]}
-    elif args.config == "gs-variants":
-        # colour (c = 8) against Bernoulli edge (p = 1/8) sparsification, 8 samplers each, on R-MAT 16;
-        # exact counts for reference
-        rp, col = G.rmat(16, 16, seed=4, device="cuda")
-        torch.cuda.synchronize()
-        g = api.Graph(rp, col)
-        out.update({"n": g.n, "m": g.m, "samplers": 8})
-        for name in ("triangle", "4-cycle"):
-            exact, te = _timed(lambda: g.exact_count(name))
-            row = {"exact": exact, "exact_s": te}
-            for label, kw in (("colour_c8", {"colors": 8}), ("edge_p0.125", {"edge_p": 0.125})):
-                r, t = _timed(lambda: g.estimate(name, scheme=api.GS, seed=5, delta=DELTA, samplers=8, **kw))
-                row[label] = {"seconds": t, "estimate": r["estimate"], "ci_half_width_99": r["ci_half_width"],
-                              "rel_err": abs(r["estimate"] - exact) / exact, "kept_matches": r["exact_count"]}
-            out[name] = row
-    print(json.dumps(out))
+def _run_row(r, t):
+    return {"time_to_converge_s": t, "t_sample_s": r["t_sample_s"], "samples": r["samples"],
+            "samples_per_s": r["samples"] / max(r["t_sample_s"], 1e-12), "estimate": r["estimate"],
+            "eps_hat": r["eps_hat"], "converged": bool(r["converged"])}
 
 
-def selector_cases(G, device="cuda"):
+def learned_vs_plain(g, api, patterns, n_max, selector=None, seed=5):
+    """Per pattern: train the proposal on plain-NS traces (2^20 samples, 3
+    epochs of Adam), then run plain NS, learned NS and the hybrid with the
+    NS/GS selector head (when given) to +-1% @ 99% on the same seed; hit rate
+    and per-sample CV^2 of plain and learned on 2^20 further samples."""
+    out = {}
+    for name in patterns:
+        prop = api.Proposal(seed=1)
+        (loss, rows), train_s = _timed(lambda: prop.train(g, name, seed=11, samples=1 << 20, epochs=3, batch=8192,
+                                                          lr=3e-3))
+        row = {"train_s": train_s, "train_rows": rows, "train_loss": loss}
+        for variant in ("plain", "learned"):
+            kw = {"mlp": prop} if variant == "learned" else {}
+            sch = api.NS_LEARNED if variant == "learned" else api.NS
+            r, t = _timed(lambda: g.estimate(name, scheme=sch, eps=EPS, delta=DELTA, seed=seed, window=WINDOW,
+                                             n_max=n_max, max_seconds=60.0, **kw))
+            row[variant] = _run_row(r, t)
+            s = g.sample_sums(name, seed=seed + 1, first=0, count=WINDOW, **kw)
+            mu = s.sum / s.n
+            row[variant]["hit_rate"] = s.hits / s.n
+            row[variant]["cv2"] = (s.sumsq / s.n - mu * mu) / (mu * mu) if mu > 0 else None
+        for label, kw in (("hybrid_cost_model", {}), ("hybrid_selector", {"selector": selector})):
+            if label == "hybrid_selector" and selector is None:
+                continue
+            r, t = _timed(lambda: g.estimate(name, scheme=api.HYBRID, eps=EPS, delta=DELTA, seed=seed,
+                                             window=WINDOW, n_max=n_max, max_seconds=60.0, colors=8, **kw))
+            row[label] = _run_row(r, t)
+            row[label]["engine"] = "GS" if r["scheme_used"] == api.GS else "NS"
+            row[label]["pilot_s"] = r["t_pilot_s"]
+        p, l = row["plain"], row["learned"]
+        row["learned_over_plain_time_per_sample"] = ((l["t_sample_s"] / max(l["samples"], 1))
+                                                     / max(p["t_sample_s"] / max(p["samples"], 1), 1e-30))
+        out[name] = row
+    return out
+
+
+def selector_cases(G, device="cuda", quick=False):
     """Synthetic (graph, pattern, colours) cases for the NS/GS selector head."""
     graphs = {
         "er-20k": G.erdos_renyi(20_000, 0.001, seed=11, device=device),
@@ -457,15 +379,19 @@ def selector_cases(G, device="cuda"):
         "cl-needle": G.chung_lu(200_000, n_cliques=100, clique_size=10, seed=15, device=device),
     }
     pats = ["triangle", "4-clique", "5-clique", "6-clique", "4-cycle", "house"]
-    return [(gname, rc, p, c) for gname, rc in graphs.items() for p in pats for c in (4, 8)]
+    cols = (4, 8)
+    if quick:
+        graphs = {k: graphs[k] for k in ("er-dense", "rmat16", "cl-needle")}
+        cols = (8,)
+    return [(gname, rc, p, c) for gname, rc in graphs.items() for p in pats for c in cols]
 
 
-def timed_selector_cases(api, G, eps=0.05, delta=0.01, time_cap=10.0):
+def timed_selector_cases(api, G, eps=0.05, delta=0.01, time_cap=10.0, quick=False):
     """Selector features of each case and which engine finished first (NS to
     eps at 1-delta, or one GS colouring)."""
     rows, labels, meta = [], [], []
     handles = {}
-    for gname, (rp, col), pname, c in selector_cases(G):
+    for gname, (rp, col), pname, c in selector_cases(G, quick=quick):
         if gname not in handles:
             handles[gname] = api.Graph(rp, col)
         g = handles[gname]
@@ -475,6 +401,8 @@ def timed_selector_cases(api, G, eps=0.05, delta=0.01, time_cap=10.0):
         gs, t_gs = _timed(lambda: g.estimate(pname, scheme=api.GS, seed=3, colors=c, max_seconds=time_cap))
         if not ns["converged"]:
             t_ns = float("inf")
+        if not gs["converged"]:
+            t_gs = float("inf")
         rows.append(info["features"])
         labels.append(1.0 if t_gs < t_ns else 0.0)
         meta.append({"graph": gname, "pattern": pname, "colors": c, "t_ns": t_ns, "t_gs": t_gs,
@@ -526,6 +454,154 @@ def selector_study(api, G, eps=0.05, delta=0.01, time_cap=10.0):
                                  "always_ns": regret(te, lambda i: False)}}
 
 
+# ------------------------------------------------------------------ companion workloads
+def companion(args):
+    """One JSON line per companion workload (1 GPU)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_03488_gb300 import api
+    from paper_2405_03488_gb300 import graphs as G
+    out = {"config": args.config}
+    if args.config == "er-triangle":
+        # G(n = 10^4, p = 0.002), triangle, 10^6 samples with seed 1; exact count for comparison
+        rp, col = G.erdos_renyi(10_000, 0.002, seed=1, device="cuda")
+        g = api.Graph(rp, col)
+        exact = g.exact_count("triangle")
+        for _ in range(args.warmup):
+            g.sample_sums("triangle", seed=1, first=0, count=10 ** 6)
+        s, t = _timed(lambda: g.sample_sums("triangle", seed=1, first=0, count=10 ** 6))
+        mu = s.sum / s.n
+        sd = ((s.sumsq / s.n - mu * mu) / s.n) ** 0.5
+        out.update({"n": g.n, "m": g.m, "samples": s.n, "seconds": t, "samples_per_s": s.n / t,
+                    "estimate": mu, "exact": exact, "rel_err": abs(mu - exact) / exact, "z": (mu - exact) / sd,
+                    "hit_rate": s.hits / s.n, "eps_hat_99": 2.5758293035489004 * sd / mu})
+        # empirical coverage of the convergence test: seeds 1..1000 at +-5% / 95% and +-1% / 99%
+        cov = {}
+        for eps, delta, R in ((0.05, 0.05, 1000), (0.01, 0.01, 1000)):
+            miss, samples, tt = 0, 0, 0.0
+            for sd_ in range(1, R + 1):
+                r, ts = _timed(lambda: g.estimate("triangle", eps=eps, delta=delta, seed=sd_, window=1 << 16))
+                miss += abs(r["estimate"] - exact) > eps * exact
+                samples += r["samples"]
+                tt += ts
+            cov["eps%g_delta%g" % (eps, delta)] = {"runs": R, "within_eps": 1 - miss / R, "nominal": 1 - delta,
+                                                   "mean_samples": samples / R, "mean_time_to_converge_s": tt / R}
+        out["coverage"] = cov
+        if not args.no_cpu_baseline:
+            og = oracle_graph(*G.to_numpy(rp, col))
+            out["cpu_oracle"] = {
+                "samples_per_s_1e6": None,
+                "time_to_converge_eps1_delta1": oracle_online_parallel(og, "triangle", 0.01, 0.01, 1, 1 << 16,
+                                                                       1 << 30, 300.0)}
+            res, wall, cores = oracle_sample(og, ["triangle"], 5.0)
+            out["cpu_oracle"]["samples_per_s_1e6"] = res["triangle"]["n"] / wall
+            out["cpu_oracle"]["cores"] = cores
+    elif args.config == "rmat24-batch":
+        # one batched run: 6 connected 4-vertex motifs (vertex-induced) and triangles, eps 0.5/1/2 %
+        rp, col = G.rmat(24, 16, seed=3, device="cuda")
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        g = api.Graph(rp, col)
+        pats, eps, names = [], [], []
+        for e in (0.005, 0.01, 0.02):
+            for nm in G.MOTIFS4 + ["triangle"]:
+                k, edges = G.pattern(nm)
+                pats.append((k, edges, nm != "triangle"))
+                eps.append(e)
+                names.append("%s@%g" % (nm, e))
+        best, tt = _timed(lambda: g.autotune(pats, seed=7, window=1 << 18))
+        for _ in range(args.warmup):
+            g.estimate_batch(pats, eps, seed=100, window=WINDOW, n_max=1 << 32, **best)
+        res, t = _timed(lambda: g.estimate_batch(pats, eps, seed=1, window=WINDOW, n_max=1 << 32, **best))
+        samples = sum(r["samples"] for r in res)
+        out.update({"n": g.n, "m": g.m, "jobs": len(pats), "autotuned": best, "autotune_s": tt,
+                    "time_to_converge_s": t, "samples": samples, "samples_per_s": samples / t,
+                    "kernel_s": res[0]["t_sample_s"], "rounds": max(r["rounds"] for r in res),
+                    "all_converged": all(r["converged"] for r in res),
+                    "per_job": {nm: {"estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"]}
+                                for nm, r in zip(names, res)}})
+    elif args.config == "chunglu-needle":
+        # Chung-Lu, 8M vertices, exponent 2.1, mean degree 20, 200 planted 12-cliques
+        rp, col = G.chung_lu(8_000_000, gamma=2.1, mean_degree=20.0, n_cliques=200, clique_size=12, seed=4,
+                             device="cuda")
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        g = api.Graph(rp, col)
+        out.update({"n": g.n, "m": g.m, "max_degree": g.max_degree})
+        og = None if args.no_cpu_baseline else oracle_graph(*G.to_numpy(rp, col))
+        for name in ("7-clique", "8-clique"):
+            row = {}
+            r, te = _timed(lambda: g.estimate(name, scheme=api.EXACT, max_seconds=120.0))
+            exact = r["exact_count"]
+            row["exact"] = {"count": exact, "seconds": te, "complete": bool(r["converged"])}
+            r, t = _timed(lambda: g.estimate(name, eps=EPS, delta=DELTA, seed=1, window=WINDOW, n_max=1 << 32,
+                                             max_seconds=60.0))
+            row["ns"] = {"seconds": t, "estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"],
+                         "converged": r["converged"], "rel_err": abs(r["estimate"] - exact) / max(exact, 1)}
+            r, t = _timed(lambda: g.estimate(name, scheme=api.GS, seed=1, colors=8))
+            row["gs_c8"] = {"seconds": t, "estimate": r["estimate"], "sparsified_count": r["exact_count"],
+                            "rel_err": abs(r["estimate"] - exact) / max(exact, 1), "preproc_s": r["t_preproc_s"]}
+            r, t = _timed(lambda: g.estimate(name, scheme=api.HYBRID, eps=EPS, delta=DELTA, seed=1, window=WINDOW,
+                                             n_max=1 << 32, max_seconds=60.0, colors=8))
+            row["hybrid"] = {"seconds": t, "scheme": {0: "NS", 1: "GS"}.get(r["scheme_used"], r["scheme_used"]),
+                             "estimate": r["estimate"], "pilot_s": r["t_pilot_s"],
+                             "rel_err": abs(r["estimate"] - exact) / max(exact, 1)}
+            prop = api.Proposal(seed=1)
+            (loss, rows), ttrain = _timed(lambda: prop.train(g, name, seed=11, samples=1 << 21, epochs=3,
+                                                             batch=8192, lr=3e-3))
+            r, t = _timed(lambda: g.estimate(name, scheme=api.NS_LEARNED, eps=EPS, delta=DELTA, seed=1,
+                                             window=WINDOW, n_max=1 << 32, max_seconds=60.0, mlp=prop))
+            row["learned"] = {"seconds": t, "train_s": ttrain, "train_rows": rows, "estimate": r["estimate"],
+                              "eps_hat": r["eps_hat"], "samples": r["samples"], "converged": r["converged"],
+                              "rel_err": abs(r["estimate"] - exact) / max(exact, 1)}
+            for variant, kw in (("plain", {}), ("learned", {"mlp": prop})):
+                sm = g.sample_sums(name, seed=9, first=0, count=1 << 22, **kw)
+                mu = sm.sum / sm.n
+                row[variant + "_cv2"] = (sm.sumsq / sm.n - mu * mu) / (mu * mu) if mu > 0 else None
+                row[variant + "_hit_rate"] = sm.hits / sm.n
+            if og is not None:
+                # the oracle's Algorithm 3 on every host core, capped at 120 s
+                row["cpu_oracle"] = oracle_online_parallel(og, name, EPS, DELTA, 1, WINDOW, 1 << 34, 120.0)
+            out[name] = row
+    elif args.config == "selector":
+        out.update(selector_study(api, G))
+    elif args.config == "complex":
+        # the paper's non-clique patterns (edge-induced), NS to +-1% at 99% on R-MAT 22
+        rp, col = make_graph(WORKLOADS["rmat22"], "cuda")
+        torch.cuda.synchronize()
+        g = api.Graph(rp, col)
+        out.update({"n": g.n, "m": g.m, "eps": EPS, "delta": DELTA})
+        for name in ("5-path", "house", "dumbbell"):
+            k, edges = G.pattern(name)
+            pat = (k, edges, False)
+            for w in range(args.warmup):
+                g.estimate(pat, eps=EPS, delta=DELTA, seed=100 + w, window=WINDOW, n_max=1 << 36, max_seconds=60.0)
+            r, t = _timed(lambda: g.estimate(pat, eps=EPS, delta=DELTA, seed=1, window=WINDOW, n_max=1 << 36,
+                                             max_seconds=60.0))
+            out[name] = {"seconds": t, "estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"],
+                         "hit_rate": r["hits"] / max(r["samples"], 1),
+                         "samples_per_s": r["samples"] / max(r["t_sample_s"], 1e-12), "converged": r["converged"]}
+    elif args.config == "gs-variants":
+        # colour (c = 8) against Bernoulli edge (p = 1/8) sparsification, 8 samplers each, on R-MAT 16;
+        # exact counts for reference
+        rp, col = G.rmat(16, 16, seed=4, device="cuda")
+        torch.cuda.synchronize()
+        g = api.Graph(rp, col)
+        out.update({"n": g.n, "m": g.m, "samplers": 8})
+        for name in ("triangle", "4-cycle"):
+            exact, te = _timed(lambda: g.exact_count(name))
+            row = {"exact": exact, "exact_s": te}
+            for label, kw in (("colour_c8", {"colors": 8}), ("edge_p0.125", {"edge_p": 0.125})):
+                r, t = _timed(lambda: g.estimate(name, scheme=api.GS, seed=5, delta=DELTA, samplers=8, **kw))
+                row[label] = {"seconds": t, "estimate": r["estimate"], "ci_half_width_99": r["ci_half_width"],
+                              "rel_err": abs(r["estimate"] - exact) / exact, "kept_matches": r["exact_count"]}
+            out[name] = row
+    print(json.dumps(out))
+
+
+
+
 # ------------------------------------------------------------------ GPU arm
 def ncu_case(args):
     """A small, self-contained case for ncu: the graph stays resident, the
@@ -535,27 +611,26 @@ def ncu_case(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2405_03488_gb300 import api
-    rp, col = make_graph("cuda")
+    wl = WORKLOADS[args.config if args.config in WORKLOADS else "rmat22"]
+    rp, col = make_graph(wl, "cuda")
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     g = api.Graph(rp, col)
     for s in range(args.warmup + args.steps):
         g.estimate(args.ncu_case, eps=EPS, delta=DELTA, seed=1 + s, window=WINDOW, n_max=WINDOW)
     torch.cuda.synchronize()
-    print(json.dumps({"ncu_case": args.ncu_case, "launches": args.warmup + args.steps, "window": WINDOW}))
+    print(json.dumps({"ncu_case": args.ncu_case, "config": args.config, "launches": args.warmup + args.steps,
+                      "window": WINDOW}))
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    if args.ncu_case:
-        ncu_case(args)
-        return
-    if args.config != "rmat22":
-        companion(args)
-        return
+def pinned_copy(t):
+    import torch
+    h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+    h.copy_(t)
+    return h
+
+
+def headline(args, wl):
     rank, world, local = dist_env()
     import numpy as np
     import torch
@@ -566,45 +641,53 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2405_03488_gb300 import api
-    from paper_2405_03488_gb300 import graphs as G
+    patterns, n_max = wl["patterns"], wl["n_max"]
 
-    rp, col = make_graph("cuda")
+    t_gen = time.perf_counter()
+    rp, col = make_graph(wl, "cuda")
     torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    torch.cuda.empty_cache()
     g = api.Graph(rp, col)
     n, m, nnz = g.n, g.m, g.nnz
+    csr_bytes = 8 * (n + 1) + 4 * nnz
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
-    def one_step(graph, step):
+    def one_step(graph, seed):
         # weak scaling: every rank runs its own estimates on its own seed stream
-        res = graph.estimate_batch(list(PATTERNS), [EPS] * len(PATTERNS), delta=DELTA,
-                                   seed=1 + step + 1000 * rank, window=WINDOW, n_max=N_MAX)
-        return dict(zip(PATTERNS, res))
+        res = graph.estimate_batch(list(patterns), [EPS] * len(patterns), delta=DELTA, seed=seed + 1000 * rank,
+                                   window=WINDOW, n_max=n_max)
+        return dict(zip(patterns, res))
 
-    for w in range(args.warmup):
-        one_step(g, w)
-    torch.cuda.synchronize()
-    barrier()
     clocks = Clocks(local)
     clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for w in range(args.warmup):
+        one_step(g, 100_000 + w)
     torch.cuda.synchronize()
-    ev0.record()
-    per_step = []
+    barrier()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    clocks.mark()
+    per_step, wall = [], []
+    evs[0].record()
     for s in range(args.steps):
-        per_step.append(one_step(g, s))
-    ev1.record()
+        t0 = time.perf_counter()
+        per_step.append(one_step(g, 1 + s))
+        evs[s + 1].record()
+        wall.append(time.perf_counter() - t0)
     torch.cuda.synchronize()
     ck = clocks.stop()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    elapsed = evs[0].elapsed_time(evs[-1]) / 1e3
     barrier()
-    samples = sum(r[p]["samples"] for r in per_step for p in PATTERNS)
+    samples = sum(r[p]["samples"] for r in per_step for p in patterns)
     # one batched call per step: kernel time, rounds and launches are per call
-    kernel_s = sum(r[PATTERNS[0]]["t_sample_s"] for r in per_step)
-    rounds = sum(max(r[p]["rounds"] for p in PATTERNS) for r in per_step)
-    launches = sum(r[PATTERNS[0]]["kernel_launches"] for r in per_step)
+    kernel_s = sum(r[patterns[0]]["t_sample_s"] for r in per_step)
+    rounds = sum(max(r[p]["rounds"] for p in patterns) for r in per_step)
+    launches = sum(r[patterns[0]]["kernel_launches"] for r in per_step)
     if world > 1:
         t = torch.tensor([elapsed], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -616,9 +699,10 @@ def main():
         samples_all = samples
     value = samples_all / elapsed
 
-    # end to end through the public API from pinned host memory
-    rp_h = rp.cpu().pin_memory()
-    col_h = col.cpu().pin_memory()
+    # end to end through the public API from pinned host memory: every step
+    # uploads the CSR, builds the index, estimates and reads the results back
+    rp_h, col_h = pinned_copy(rp), pinned_copy(col)
+    rp_np, col_np = rp_h.numpy().view(np.uint64), col_h.numpy().view(np.uint32)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
@@ -626,65 +710,100 @@ def main():
     t_load, t_est = [], []
     for s in range(args.steps):
         ta = time.perf_counter()
-        gh = api.Graph(rp_h.numpy().view(np.uint64), col_h.numpy().view(np.uint32))
+        gh = api.Graph(rp_np, col_np)
         tb = time.perf_counter()
-        r = one_step(gh, s)
+        r = one_step(gh, 1 + s)
         t_load.append(tb - ta)
         t_est.append(time.perf_counter() - tb)
         gh.close()
-        e2e_samples += sum(r[p]["samples"] for p in PATTERNS)
+        e2e_samples += sum(r[p]["samples"] for p in patterns)
         # per graph launch the control word (16 B) comes back, at the end the job states
-        e2e_d2h += 16 * ((max(r[p]["rounds"] for p in PATTERNS) + 3) // 4) + 128 * len(PATTERNS) + 32
+        e2e_d2h += 16 * ((max(r[p]["rounds"] for p in patterns) + 3) // 4) + 128 * len(patterns) + 32
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
-    e2e = {"value": e2e_samples * world / e2e_t, "unit": "samples/s",
-           "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz, "d2h_bytes_per_step": e2e_d2h // args.steps,
+    e2e = {"value": e2e_samples * world / e2e_t, "unit": "samples/s", "h2d_bytes_per_step": csr_bytes,
+           "d2h_bytes_per_step": e2e_d2h // args.steps,
            "load_ms_per_step": [1e3 * x for x in t_load], "estimate_ms_per_step": [1e3 * x for x in t_est]}
 
-    learned = learned_vs_plain(g, api) if (rank == 0 and not args.no_learned) else None
+    learned = None
+    if rank == 0 and not args.no_learned:
+        from paper_2405_03488_gb300 import graphs as G
+        (rows_s, labels_s, _, handles), t_cases = _timed(lambda: timed_selector_cases(api, G, time_cap=3.0,
+                                                                                      quick=True))
+        (sel, sel_loss), t_train = _timed(lambda: train_selector(api, rows_s, labels_s,
+                                                                 next(iter(handles.values()))))
+        for h_ in handles.values():
+            h_.close()
+        del handles
+        torch.cuda.empty_cache()
+        learned = learned_vs_plain(g, api, patterns, n_max, selector=sel)
+        learned["selector_training"] = {"cases": len(rows_s), "gs_faster": int(sum(labels_s)),
+                                        "cases_s": t_cases, "train_s": t_train, "train_loss": sel_loss}
     if rank != 0:
         return
     last = per_step[-1]
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "m": m, "patterns": list(PATTERNS), "eps": EPS,
-                       "delta": DELTA, "window": WINDOW, "n_max": N_MAX,
-                       "l2": "inputs larger than L2 (CSR %.2f GB vs 129 MB L2)" % ((8 * (n + 1) + 4 * nnz) / 1e9)},
-            "time_to_converge_s": {"batch": last[PATTERNS[0]]["t_total_s"]},
-            "samples_to_converge": {p: last[p]["samples"] for p in PATTERNS},
-            "estimate": {p: last[p]["estimate"] for p in PATTERNS},
-            "eps_hat": {p: last[p]["eps_hat"] for p in PATTERNS},
-            "hit_rate": {p: last[p]["hits"] / max(1, last[p]["samples"]) for p in PATTERNS},
+            "config": {"workload": wl["workload"], "n": n, "m": m, "patterns": list(patterns), "eps": EPS,
+                       "delta": DELTA, "window": WINDOW, "n_max": n_max,
+                       "l2": "inputs larger than L2 (CSR %.2f GB vs 129 MB L2)" % (csr_bytes / 1e9)},
+            "step_ms": step_ms, "step_wall_ms": [1e3 * x for x in wall],
+            "sampler_ms_per_step": [1e3 * r[patterns[0]]["t_sample_s"] for r in per_step],
+            "graph_generation_s": t_gen,
+            "time_to_converge_s": {"batch": last[patterns[0]]["t_total_s"]},
+            "samples_to_converge": {p: last[p]["samples"] for p in patterns},
+            "estimate": {p: last[p]["estimate"] for p in patterns},
+            "eps_hat": {p: last[p]["eps_hat"] for p in patterns},
+            "hit_rate": {p: last[p]["hits"] / max(1, last[p]["samples"]) for p in patterns},
             "e2e": e2e, "gpu_launches": int(launches), "clocks": ck, "learned_vs_plain": learned}
 
     peak, peak_kind = measured_peaks()
     roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
-            "traffic": ncu_traffic(), "kernel": "ns_batch_kernel<INTERSECT, compact>", "peak_kind": peak_kind}
+            "traffic": ncu_traffic(args.config), "kernel": "ns_batch_kernel<INTERSECT, compact>",
+            "peak_kind": peak_kind}
     if world == 1 and not args.no_cpu_baseline:
-        ores, wall, cores = oracle_sample(*G.to_numpy(rp, col), args.cpu_seconds)
+        og = oracle_graph(rp_np, col_np)
+        ores, owall, cores = oracle_sample(og, patterns, args.cpu_seconds)
         cpu_n = sum(v["n"] for v in ores.values())
-        line["cpu_baseline"] = {"value": cpu_n / wall, "unit": "samples/s", "cores": cores, "kind": "oracle",
+        line["cpu_baseline"] = {"value": cpu_n / owall, "unit": "samples/s", "cores": cores, "kind": "oracle",
                                 "sample": "%d samples (prefix of each pattern's seed-1 stream, %s) split over %d "
-                                          "spawned processes" % (cpu_n, "+".join(PATTERNS), cores)}
+                                          "threads" % (cpu_n, "+".join(patterns), cores)}
         # algorithmic bytes per sample from the oracle's per-sample accounting
-        bbar = {p: ores[p]["bytes"] / ores[p]["n"] for p in PATTERNS}
-        algo_bytes = sum(bbar[p] * r[p]["samples"] for r in per_step for p in PATTERNS)
+        bbar = {p: ores[p]["bytes"] / ores[p]["n"] for p in patterns}
+        algo_bytes = sum(bbar[p] * r[p]["samples"] for r in per_step for p in patterns)
         achieved = algo_bytes / kernel_s / 1e9
         roof.update({"achieved": achieved, "frac": achieved / peak if peak else None,
-                     "bytes_per_sample": bbar, "launches": int(rounds),
+                     "bytes_per_sample": bbar, "bytes_source": "oracle prefix sample", "launches": int(rounds),
                      "avg_launch_ms": 1e3 * kernel_s / max(1, rounds)})
         # the random-access roofline of the same pattern: dependent chains of 32-byte
         # sector reads over a buffer the size of the CSR (secondary to the copy peak)
-        csr = 8 * (n + 1) + 4 * nnz
-        gather = {"buffer_bytes": csr}
+        gather = {"buffer_bytes": csr_bytes}
         for chain in (3, 6):
-            r_rand = api.gather_probe(csr, chain=chain) / 1e9
+            r_rand = api.gather_probe(csr_bytes, chain=chain) / 1e9
             gather["chain%d_GBps" % chain] = r_rand
             gather["frac_chain%d" % chain] = achieved / r_rand
         roof["gather_roofline"] = gather
+        if args.config == "rmat22":
+            # the oracle's own time to converge, Algorithm 3 on every host core
+            line["cpu_time_to_converge"] = {p: oracle_online_parallel(og, p, EPS, DELTA, 1, WINDOW, n_max, 300.0)
+                                            for p in patterns}
     line["roofline"] = roof
     print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.ncu_case:
+        ncu_case(args)
+        return
+    if args.config in WORKLOADS:
+        headline(args, WORKLOADS[args.config])
+    else:
+        companion(args)
 
 
 if __name__ == "__main__":
