@@ -12,6 +12,10 @@
  *   - Sec. 4.1 / Eq. (equ:error) / Theorem 1 / Algorithm 3: online convergence
  *     detection with running sum and squared sum, var = sq/n - mu^2,
  *     sigma = sqrt(var/n), eps_hat = Phi^-1(1 - delta/2) * sigma / mu.
+ *   - Sec. 2.2.1 / Algorithm 1 and Sec. 4.2: NS-base, lazy verify: each vertex
+ *     is drawn from the union of its pattern neighbours' lists with weight
+ *     factor |U_j|, and every constraint is checked only after all k draws
+ *     (closure check); see og_union and og_closure.
  *   - Sec. 4.2 / Algorithm 4 / Lemma 1: eager verify ("NS-prune"): each vertex
  *     is drawn uniformly from a candidate set that already folds in every
  *     pattern edge to earlier vertices and the symmetry-breaking bounds; the
@@ -338,7 +342,7 @@ int og_plan_build(int k, const uint32_t *pattern_adj, int induced, og_plan *p)
 /* ------------------------------------------------------------------------- */
 /* Sampler (Algorithm 4 generalised; Lemma 1).                              */
 /* ------------------------------------------------------------------------- */
-enum { OG_INTERSECT = 0, OG_CHECK = 1, OG_LEARNED = 2 };
+enum { OG_INTERSECT = 0, OG_CHECK = 1, OG_LEARNED = 2, OG_LAZY = 3 };
 
 typedef struct {
     uint64_t factor[OG_MAXK];  /* factor[0] = M; factor[j] = |S_j| (|L_j|, or A) */
@@ -409,6 +413,50 @@ static uint64_t og_cand(const og_graph *g, const og_plan *p, const uint32_t *v, 
         }
     }
     return cnt;
+}
+
+/* NS-base (Sec. 2.2.1, Algorithm 1; the lazy verify of Sec. 4.2): the
+ * candidates of position j are the union of its back-neighbours' lists,
+ * U_j = N(v_a) u N(v_b) u ... (the paper's 4-cycle example draws v3 from
+ * N(v0) u N(v2)), with no other condition.  Order: the back-neighbours by
+ * position ascending; the first one's list in full, then each later list's
+ * entries that no earlier list holds, each list in ascending order.
+ * Written into out; returns |U_j|. */
+static uint64_t og_union(const og_graph *g, const og_plan *p, const uint32_t *v, int j, uint32_t *out)
+{
+    uint64_t cnt = 0;
+    for (int i = 0; i < j; i++) {
+        if (!((p->adj[j] >> i) & 1u)) continue;
+        for (uint64_t e = g->row_ptr[v[i]]; e < g->row_ptr[v[i] + 1]; e++) {
+            uint32_t x = g->col[e];
+            int seen = 0;
+            for (int q = 0; q < i; q++)
+                if (((p->adj[j] >> q) & 1u) && og_adjacent(g, v[q], x)) seen = 1;
+            if (seen) continue;
+            if (out) out[cnt] = x;
+            cnt++;
+        }
+    }
+    return cnt;
+}
+
+/* The closure check NS-base defers to the end of a sample: the k drawn
+ * vertices are distinct, every pattern edge is a graph edge, every pattern
+ * non-edge is a non-edge when vertex-induced, and every symmetry-breaking
+ * restriction holds. */
+static int og_closure(const og_graph *g, const og_plan *p, const uint32_t *v)
+{
+    for (int j = 1; j < p->k; j++)
+        for (int i = 0; i < j; i++) {
+            if (v[i] == v[j]) return 0;
+            int edge = (int)((p->adj[j] >> i) & 1u);
+            int adj = og_adjacent(g, v[i], v[j]);
+            if (edge && !adj) return 0;
+            if (!edge && p->induced && adj) return 0;
+        }
+    for (int r = 0; r < p->nres; r++)
+        if (!(v[p->res_lo[r]] < v[p->res_hi[r]])) return 0;
+    return 1;
 }
 
 /* Map the first-edge index e to (v0, v1). */
@@ -506,14 +554,23 @@ int og_sample(const og_graph *g, const og_plan *p, const uint64_t *r, int mode,
     memset(rec, 0, sizeof(*rec));
     for (int j = 0; j < OG_MAXK; j++) rec->vert[j] = 0xFFFFFFFFu;
     uint32_t v[OG_MAXK];
-    uint64_t M = p->oriented ? og_graph_m(g) : g->nnz;
+    /* NS-base draws the first edge from all 2m directed entries: the
+     * restriction between v0 and v1, like every other, waits for the closure */
+    int oriented = (mode == OG_LAZY) ? 0 : p->oriented;
+    uint64_t M = oriented ? og_graph_m(g) : g->nnz;
     rec->factor[0] = M;
     if (M == 0) {
         rec->depth = 0;
         return 0;
     }
     uint64_t e = og_index_map(r[0], M);
-    og_first_edge(g, p, e, &v[0], &v[1]);
+    if (oriented) {
+        og_first_edge(g, p, e, &v[0], &v[1]);
+    } else {
+        og_plan q = *p;
+        q.oriented = 0;
+        og_first_edge(g, &q, e, &v[0], &v[1]);
+    }
     rec->vert[0] = v[0];
     rec->vert[1] = v[1];
     double w = (double)M;
@@ -522,7 +579,14 @@ int og_sample(const og_graph *g, const og_plan *p, const uint64_t *r, int mode,
     for (int j = 2; j < p->k; j++) {
         uint64_t size, pick;
         uint32_t x;
-        if (mode == OG_CHECK) {
+        if (mode == OG_LAZY) {
+            size = og_union(g, p, v, j, buf);      /* never empty: v_a has a neighbour */
+            rec->factor[j] = size;
+            pick = og_index_map(r[j - 1], size);
+            x = buf[pick];
+            w = w * (double)size;
+            if (__builtin_mul_overflow(wu, size, &wu)) overflow = 1;
+        } else if (mode == OG_CHECK) {
             int pb = og_last_back(p, j);
             uint32_t lo = 0;
             int has = og_lower(p, v, j, &lo);
@@ -576,8 +640,9 @@ int og_sample(const og_graph *g, const og_plan *p, const uint64_t *r, int mode,
         v[j] = x;
         rec->vert[j] = x;
     }
-    rec->hit = 1;
     rec->depth = (uint8_t)p->k;
+    if (mode == OG_LAZY && !og_closure(g, p, v)) return 0;   /* a miss after all k draws */
+    rec->hit = 1;
     rec->w_f64 = w;
     rec->w_u64 = (mode == OG_LEARNED) ? 0 : (overflow ? 0 : wu);
     rec->overflow = (uint8_t)overflow;
@@ -628,6 +693,20 @@ static double og_log2ceil(uint64_t n)
 double og_sample_bytes(const og_graph *g, const og_plan *p, int mode, const og_record *rec)
 {
     double sec = 1.0;
+    if (mode == OG_LAZY) {
+        /* NS-base: each step reads its back-neighbours' lists in full; the
+         * closure reads one binary search per checked pair (i, j) */
+        if (rec->depth < p->k) return 32.0 * sec;
+        for (int j = 2; j < p->k; j++)
+            for (int i = 0; i < j; i++)
+                if ((p->adj[j] >> i) & 1u) sec += 1.0 + og_sectors(g->row_ptr[rec->vert[i]], g->row_ptr[rec->vert[i] + 1]);
+        for (int j = 1; j < p->k; j++)
+            for (int i = 0; i < j; i++) {
+                int edge = (int)((p->adj[j] >> i) & 1u);
+                if (edge || p->induced) sec += 1.0 + og_log2ceil(og_deg(g, rec->vert[i]));
+            }
+        return 32.0 * sec;
+    }
     int steps = rec->hit ? p->k : rec->depth + 1;
     uint32_t v[OG_MAXK];
     for (int i = 0; i < OG_MAXK; i++) v[i] = rec->vert[i];
@@ -695,6 +774,26 @@ int og_ns_run(const og_graph *g, const og_plan *p, int mode, const og_mlp *mlp,
         acc->sumsq += x * x;
         if (want_bytes) acc->bytes += og_sample_bytes(g, p, mode, &rec);
         if (recs) recs[s - first] = rec;
+    }
+    free(buf);
+    free(buf2);
+    return 0;
+}
+
+/* Per-sample algorithmic bytes of samples [first, first+count) into out. */
+int og_ns_bytes(const og_graph *g, const og_plan *p, int mode, const og_mlp *mlp,
+                uint64_t seed, uint32_t slot, uint64_t first, uint64_t count, double *out)
+{
+    uint64_t md = og_maxdeg(g) + 1;
+    uint32_t *buf = (uint32_t *)malloc(sizeof(uint32_t) * md);
+    uint32_t *buf2 = (uint32_t *)malloc(sizeof(uint32_t) * md);
+    if (!buf || !buf2) { free(buf); free(buf2); return -1; }
+    for (uint64_t s = first; s < first + count; s++) {
+        uint64_t r[OG_MAXK];
+        for (int t = 0; t + 1 < p->k; t++) r[t] = og_choice_word(seed, s, slot, 0, (uint32_t)t);
+        og_record rec;
+        og_sample(g, p, r, mode, mlp, buf, buf2, &rec);
+        out[s - first] = og_sample_bytes(g, p, mode, &rec);
     }
     free(buf);
     free(buf2);

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 MAXK = 12
 MAXRES = 66
 
-INTERSECT, CHECK, LEARNED = 0, 1, 2
+INTERSECT, CHECK, LEARNED, LAZY = 0, 1, 2, 3
 
 
 class Plan(C.Structure):
@@ -120,6 +120,8 @@ def lib():
             L.og_ns_run.restype = i32
             L.og_ns_run.argtypes = [C.c_void_p, P(Plan), i32, P(MLP16), u64, u32, u64, u64,
                                     P(Sums), C.c_void_p, i32]
+            L.og_ns_bytes.restype = i32
+            L.og_ns_bytes.argtypes = [C.c_void_p, P(Plan), i32, P(MLP16), u64, u32, u64, u64, C.c_void_p]
             L.og_phi_inv.restype = dbl
             L.og_phi_inv.argtypes = [dbl]
             L.og_error_of.argtypes = [dbl, dbl, u64, dbl, P(dbl), P(dbl), P(dbl)]
@@ -267,6 +269,16 @@ def ns_run(g, p, seed, first, count, mode=INTERSECT, mlp=None, slot=0, trace=Fal
     if rc != 0:
         raise MemoryError("oracle run failed")
     return acc, recs
+
+
+def ns_bytes(g, p, seed, first, count, mode=INTERSECT, mlp=None, slot=0):
+    """Algorithmic bytes of each sample of [first, first+count) (float64 array)."""
+    out = np.zeros(count, dtype=np.float64)
+    rc = lib().og_ns_bytes(g.h, C.byref(p), mode, C.byref(mlp.c) if mlp else None, seed, slot, first, count,
+                           out.ctypes.data)
+    if rc != 0:
+        raise MemoryError("oracle run failed")
+    return out
 
 
 def ns_online(g, p, eps, delta, seed, window, n_min=None, n_max=10**9, mode=INTERSECT, mlp=None, slot=0):

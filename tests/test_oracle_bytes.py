@@ -164,3 +164,20 @@ def test_vertex_induced_step_reads_the_non_neighbour(g):
     p, rec, b = run(g, WEDGE, [word(20, 50), word(1, 4)], induced=False)
     assert rec.hit == 1 and verts(rec, 3) == [3, 1, 5]
     assert b == 128.0
+
+
+def test_lazy_mode_reads_whole_lists_and_one_search_per_closing_pair(g):
+    # NS-base, triangle: first edge from the 50 directed entries; (1 -> 3) is entry
+    # row_ptr[1] + 2 = 13.  U_2 = N(1) then N(3) minus N(1) = [0 2 3 4 6 9 | 1 5], size 8.
+    # step 2 reads both lists whole: N(1) = col[11, 17): sectors 1..2 -> 1 + 2
+    #                                N(3) = col[19, 25): sectors 2..3 -> 1 + 2
+    # closure, one search per pattern edge (i, j), i < j, in N(v_i), ceil(log2(6 + 1)) = 3:
+    #   (0, 1) in N(1): 1 + 3;  (0, 2) in N(1): 1 + 3;  (1, 2) in N(3): 1 + 3
+    # total 1 + 3 + 3 + 12 = 19 sectors = 608 bytes, hit or miss alike
+    TRI = (3, [(0, 1), (1, 2), (0, 2)])
+    p, rec, b = run(g, TRI, [word(13, 50), word(4, 8)], mode=O.LAZY)
+    assert rec.hit == 1 and verts(rec, 3) == [1, 3, 6] and rec.factor[2] == 8 and rec.w_u64 == 400
+    assert b == 608.0
+    p, rec, b = run(g, TRI, [word(13, 50), word(6, 8)], mode=O.LAZY)    # x = 1 = v0: closure fails
+    assert rec.hit == 0 and rec.depth == 3 and verts(rec, 3) == [1, 3, 1]
+    assert b == 608.0

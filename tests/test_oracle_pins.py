@@ -156,7 +156,7 @@ def enumerate_tree(g, p, mode, mlp=None):
     """Every path of the sampler, driven by explicit choice words: returns the
     hit leaves as (vertices, probability, record) and the total probability."""
     k = p.k
-    M = g.m if p.oriented else g.nnz
+    M = g.m if (p.oriented and mode != O.LAZY) else g.nnz
     leaves = []
     total = [Fraction(0)]
 
@@ -188,7 +188,7 @@ def enumerate_tree(g, p, mode, mlp=None):
         if rec.hit and j == k - 1:
             leaves.append((tuple(rec.vert[:k]), prob, rec))
             total[0] += prob
-        elif rec.hit or rec.depth > j:
+        elif (rec.hit or rec.depth > j) and j < k - 1:
             walk(r, j + 1, prob)
         else:
             total[0] += prob
@@ -242,7 +242,7 @@ TREE_CASES = [("triangle", False), ("4-clique", False), ("4-cycle", False), ("4-
 
 
 @pytest.mark.parametrize("name,induced", TREE_CASES)
-@pytest.mark.parametrize("mode", [O.INTERSECT, O.CHECK, O.LEARNED])
+@pytest.mark.parametrize("mode", [O.INTERSECT, O.CHECK, O.LEARNED, O.LAZY])
 def test_sampling_tree_is_exact(name, induced, mode):
     """Lemma 1: each match is reached by exactly one path, whose probability is
     the inverse of its weight; so the hit leaves are exactly the matches and
@@ -275,6 +275,8 @@ def exact_moments(g, p, mode, mlp=None):
 
 @pytest.mark.parametrize("name,induced,mode", [("4-clique", False, O.INTERSECT),
                                                ("4-cycle", False, O.CHECK),
+                                               ("4-cycle", False, O.LAZY),
+                                               ("tailed-triangle", True, O.LAZY),
                                                ("house", False, O.INTERSECT),
                                                ("diamond", True, O.LEARNED)])
 def test_unbiased_over_philox_samples(name, induced, mode):
@@ -612,3 +614,49 @@ def test_learned_large_sets_fall_back_to_uniform_and_stay_unbiased():
     mean = acc.sum / N
     sd = math.sqrt(max(acc.sumsq / N - mean * mean, 0.0) / N)
     assert abs(mean - C) < 5 * sd + 1e-9 * C
+
+
+# ------------------------------------------------------------------ NS-base (lazy verify)
+def test_lazy_triangles_in_complete_graph_closed_form():
+    """NS-base on K_n, triangle: the first edge is one of the n(n-1) directed
+    entries, U_2 = N(v0) u N(v1) is every vertex (n of them), so every sample
+    weighs n^2 (n-1), and a sample hits iff v0 < v1 < v2: C(n, 3) of the
+    n^2 (n-1) equally likely paths.  The eager sampler misses only when the
+    oriented first edge ends at the top vertex: n - 1 of the C(n, 2) edges."""
+    n = 7
+    rp, col = G.complete(n)
+    g = og(rp, col)
+    p = O.plan(*G.pattern("triangle"))
+    W = n * n * (n - 1)
+    leaves, total = enumerate_tree(g, p, O.LAZY)
+    assert total == 1 and len(leaves) == math.comb(n, 3)
+    for _, prob, rec in leaves:
+        assert prob == Fraction(1, W) and rec.w_u64 == W
+    N = 60_000
+    acc, recs = O.ns_run(g, p, seed=3, first=0, count=N, mode=O.LAZY, trace=True)
+    assert np.all(recs["factor"][:, 2] == n) and np.all(recs["factor"][:, 0] == n * (n - 1))
+    q = math.comb(n, 3) / W
+    assert abs(acc.hits / N - q) < 5 * math.sqrt(q * (1 - q) / N)
+    eager, _ = O.ns_run(g, p, seed=3, first=0, count=N)
+    qe = 1 - (n - 1) / math.comb(n, 2)
+    assert abs(eager.hits / N - qe) < 5 * math.sqrt(qe * (1 - qe) / N)
+
+
+def test_lazy_union_order_and_closure_on_a_path():
+    """A 4-path graph 0-1-2-3 and the 4-cycle pattern (order 0-1-2-3: v2 from
+    N(v1), v3 from N(v0) u N(v2)): from the first edge (1, 0), N(v1 = 0) = {1}
+    gives v2 = 1, a repeated vertex the lazy sampler only rejects at the end;
+    from (1, 2), N(2) = {1, 3} and U_3 = N(1) u N(3) = {0, 2} then {2} again:
+    in list order 0, 2 (N(1) = {0, 2} first, N(3) = {2} adds nothing)."""
+    rp, col = G.from_edge_list(4, [(0, 1), (1, 2), (2, 3)])
+    g = og(rp, col)
+    p = O.plan(*G.pattern("4-cycle"))
+    assert list(p.order) [:4] == [0, 1, 2, 3]
+    # directed entries: 0->1 (0), 1->0 (1), 1->2 (2), 2->1 (3), 2->3 (4), 3->2 (5)
+    rec = O.sample(g, p, [_ceil_word(1, 6), 0, 0], mode=O.LAZY)
+    assert rec.hit == 0 and rec.depth == 4 and [rec.vert[i] for i in range(3)] == [1, 0, 1]
+    assert [rec.factor[j] for j in range(4)] == [6, 0, 1, 2]
+    rec = O.sample(g, p, [_ceil_word(2, 6), _ceil_word(1, 2), _ceil_word(1, 2)], mode=O.LAZY)
+    assert [rec.vert[i] for i in range(4)] == [1, 2, 3, 2] and rec.factor[3] == 2 and rec.hit == 0
+    rec = O.sample(g, p, [_ceil_word(2, 6), _ceil_word(1, 2), _ceil_word(0, 2)], mode=O.LAZY)
+    assert [rec.vert[i] for i in range(4)] == [1, 2, 3, 0] and rec.hit == 0    # 3-0 is not an edge
