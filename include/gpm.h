@@ -105,7 +105,10 @@ typedef struct {
                                Bernoulli edge sparsification keeping each edge with this
                                probability (Algorithm 2; edge-induced patterns only) */
     uint32_t samplers;      /* GS: independent sparsifications averaged (default 1) */
-    uint32_t pad_;
+    uint32_t bytes_sample;  /* NS, NS_LEARNED, batches: after the run, trace this many samples from
+                               the start of the run's stream and report their mean algorithmic
+                               bytes in gpm_result.algo_bytes_per_sample (0 = skip; not counted
+                               in t_total_s) */
 } gpm_config;
 
 /* What the hybrid choice saw (Sec. 4.3-4.4, 5.1): the pilot's sample count
@@ -138,6 +141,8 @@ typedef struct {
     uint64_t exact_count;   /* GS: count on the sparsified graph(s), summed over the samplers;
                                EXACT: the count */
     uint64_t kernel_launches; /* kernels this call launched */
+    double algo_bytes_per_sample; /* mean of gpm_sample_record.sectors x 32 over the first
+                               cfg->bytes_sample samples of the run (0 when not asked for) */
 } gpm_result;
 
 /* One sample's path, for parity checks and training traces. */
@@ -147,7 +152,17 @@ typedef struct {
     double w_f64;               /* weight as a left-to-right FP64 product, 0 on a miss */
     uint32_t vert[GPM_MAX_K];   /* matched vertices in matching order, 0xFFFFFFFF past the depth */
     uint32_t aux[GPM_MAX_K];    /* learned: score a_x of the chosen vertex at step j */
-    uint8_t hit, depth, overflow, pad[5];
+    uint8_t hit, depth, overflow, pad;
+    uint32_t sectors;           /* algorithmic 32-byte sectors of the sample's path (Sec. 4.2's
+                                   per-step set reads): 1 for the first edge; per step j taken and
+                                   per list the candidate-set definition references there (every
+                                   back-neighbour, and every other earlier vertex when vertex-
+                                   induced; only N(v_{j-1}) when S_j extends S_{j-1} by one
+                                   adjacency under the same bounds), 1 for its row_ptr pair plus
+                                   the sectors its part above the step's lower bound spans; CHECK:
+                                   per step 1 + a bound search ceil(log2(d + 1)) when bounded, and
+                                   when L_j is not empty 1 for the drawn entry plus, per other
+                                   referenced list, 1 + ceil(log2(d + 1)) */
 } gpm_sample_record;
 
 /* Totals of a fixed block of samples. */

@@ -42,7 +42,7 @@ class Config(C.Structure):
                 ("max_seconds", C.c_double), ("colors", C.c_uint32), ("slot", C.c_uint32),
                 ("verify", C.c_uint32), ("grid_blocks", C.c_uint32), ("block_warps", C.c_uint32),
                 ("cap", C.c_uint32), ("mlp", C.POINTER(MLP)), ("selector", C.POINTER(MLP)),
-                ("edge_p", C.c_double), ("samplers", C.c_uint32), ("pad_", C.c_uint32)]
+                ("edge_p", C.c_double), ("samplers", C.c_uint32), ("bytes_sample", C.c_uint32)]
 
 
 class HybridInfo(C.Structure):
@@ -62,7 +62,7 @@ class Result(C.Structure):
                 ("hits", C.c_uint64), ("rounds", C.c_uint64), ("scheme_used", C.c_int32),
                 ("converged", C.c_int32), ("t_total_s", C.c_double), ("t_pilot_s", C.c_double),
                 ("t_preproc_s", C.c_double), ("t_sample_s", C.c_double), ("exact_count", C.c_uint64),
-                ("kernel_launches", C.c_uint64)]
+                ("kernel_launches", C.c_uint64), ("algo_bytes_per_sample", C.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -71,7 +71,7 @@ class Result(C.Structure):
 class SampleRecord(C.Structure):
     _fields_ = [("factor", C.c_uint64 * MAX_K), ("w_u64", C.c_uint64), ("w_f64", C.c_double),
                 ("vert", C.c_uint32 * MAX_K), ("aux", C.c_uint32 * MAX_K), ("hit", C.c_uint8),
-                ("depth", C.c_uint8), ("overflow", C.c_uint8), ("pad", C.c_uint8 * 5)]
+                ("depth", C.c_uint8), ("overflow", C.c_uint8), ("pad", C.c_uint8), ("sectors", C.c_uint32)]
 
 
 class Sums(C.Structure):

@@ -13,7 +13,7 @@ from ._lib import (DEVICE_PTRS, EXACT, GS, HYBRID, NS, NS_LEARNED,  # noqa: F401
 
 RECORD_DTYPE = np.dtype([("factor", np.uint64, _lib.MAX_K), ("w_u64", np.uint64), ("w_f64", np.float64),
                          ("vert", np.uint32, _lib.MAX_K), ("aux", np.uint32, _lib.MAX_K), ("hit", np.uint8),
-                         ("depth", np.uint8), ("overflow", np.uint8), ("pad", np.uint8, 5)])
+                         ("depth", np.uint8), ("overflow", np.uint8), ("pad", np.uint8), ("sectors", np.uint32)])
 assert RECORD_DTYPE.itemsize == C.sizeof(_lib.SampleRecord)
 PARTIAL_DTYPE = np.dtype([("sum", np.float64), ("sumsq", np.float64), ("hits", np.uint64), ("n", np.uint64)])
 assert PARTIAL_DTYPE.itemsize == C.sizeof(_lib.Partial)

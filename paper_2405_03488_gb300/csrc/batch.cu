@@ -413,6 +413,13 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
         all = all && J.converged;
     }
     cleanup();
+    if (cfg && cfg->bytes_sample && (status == GPM_OK || status == GPM_ERR_NOT_CONVERGED)) {
+        for (uint32_t q = 0; q < nj; q++) {
+            const gpm_status sb = algo_bytes_mean(h, plans[q], mode, seed, jobs[q].slot, cfg, cfg->bytes_sample,
+                                                  &results[q].algo_bytes_per_sample);
+            if (sb != GPM_OK) return sb;
+        }
+    }
     if (status == GPM_OK && !all) {
         status = GPM_ERR_NOT_CONVERGED;
         set_error("n_max reached before eps_hat <= eps for at least one job");

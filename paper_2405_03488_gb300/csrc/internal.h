@@ -134,6 +134,8 @@ gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colo
 double normal_quantile(double p);
 gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const double *eps, double delta,
                           uint64_t seed, const gpm_config *cfg, gpm_result *results, int mode);
+gpm_status algo_bytes_mean(gpm_graph *h, const Plan &p, int mode, uint64_t seed, uint32_t slot,
+                           const gpm_config *cfg, uint64_t count, double *out);
 }  // namespace gpm
 
 // The opaque handle.

@@ -50,6 +50,63 @@
 
 namespace gpm {
 
+// Algorithmic 32-byte sectors of a finished sample (trace mode only): the
+// graph data the candidate-set definition of Sec. 4.2 references on the path
+// the sample took, independent of how the kernel actually read it.  All
+// lanes call it; v[] holds the matched vertices, fac[] the step factors.
+//   first edge: 1 sector;
+//   step j (every step taken; a miss at j ends after step j):
+//     INTERSECT: per referenced list L (the back-neighbours of j, and every
+//       earlier position when vertex-induced; only N(v_{j-1}) when S_j is
+//       S_{j-1} cut by N(v_{j-1}): same earlier neighbours plus j-1, and every
+//       lower bound of j-1 also bounds j), 1 sector for its row_ptr pair plus
+//       the sectors spanned by its entries above the step's lower bound;
+//     CHECK: 1 for the row_ptr pair of the drawn-from list N(v_p), a bound
+//       search of ceil(log2(d + 1)) sectors when bounded, and when L_j is not
+//       empty 1 for the drawn entry plus 1 + ceil(log2(d + 1)) per other
+//       referenced list (its membership search).
+__device__ __forceinline__ uint32_t log2_ceil_plus1(uint64_t d) { return 64u - (uint32_t)__clzll((long long)d); }
+
+template <int MODE>
+__device__ uint32_t algo_sectors(const DGraph &g, const Plan &p, const uint32_t *v, const uint64_t *fac, int depth,
+                                 bool hit) {
+    uint32_t sec = 1;
+    const int steps = hit ? p.k : depth + 1;
+    for (int j = 2; j < steps && j < p.k; j++) {
+        const uint32_t lm = p.lower[j];
+        uint32_t lo = 0;
+        for (int i = 0; i < j; i++)
+            if ((lm >> i) & 1u) lo = v[i] > lo ? v[i] : lo;
+        if (MODE == MODE_CHECK) {
+            const int pb = (int)p.last_back[j];
+            const uint64_t dpb = __ldg(g.row_ptr + v[pb] + 1) - __ldg(g.row_ptr + v[pb]);
+            sec += 1u + (lm ? log2_ceil_plus1(dpb) : 0u);
+            if (fac[j] == 0) continue;
+            sec += 1u;
+            for (int i = 0; i < j; i++) {
+                const bool edge = (p.back[j] >> i) & 1u;
+                if (i == pb || (!edge && !p.induced)) continue;
+                const uint64_t di = __ldg(g.row_ptr + v[i] + 1) - __ldg(g.row_ptr + v[i]);
+                sec += 1u + log2_ceil_plus1(di);
+            }
+            continue;
+        }
+        const uint32_t below = (1u << (j - 1)) - 1u;
+        const bool reuse = j >= 3 && (p.back[j] & below) == p.back[j - 1] && ((p.back[j] >> (j - 1)) & 1u) &&
+                           (p.lower[j - 1] & ~lm) == 0;
+        for (int i = 0; i < j; i++) {
+            const bool edge = (p.back[j] >> i) & 1u;
+            if (!edge && !p.induced) continue;
+            if (reuse && i != j - 1) continue;
+            const uint64_t rb = __ldg(g.row_ptr + v[i]), re = __ldg(g.row_ptr + v[i] + 1);
+            const uint64_t b = lm ? rb + warp_upper_bound(g.col + rb, re - rb, lo) : rb;
+            if (re > b) sec += 1u + (uint32_t)((re * 4 + 31) / 32 - (b * 4) / 32);
+            else sec += 1u;
+        }
+    }
+    return sec;
+}
+
 template <int MODE, bool TRACE>
 __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOCKS) ns_kernel(const DGraph g, const Plan p, const RunArgs a) {
     extern __shared__ uint64_t smem64[];
@@ -79,6 +136,8 @@ __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOC
             }
             if (TRACE) {
                 __syncwarp();
+                const uint32_t sectors = algo_sectors<MODE == MODE_CHECK ? MODE_CHECK : MODE_INTERSECT>(
+                    g, p, wm.v, wm.fac, r.hit ? p.k : r.depth, r.hit);
                 gpm_sample_record *rec = a.trace + (s - a.first);
                 if (lane < kMaxK) {
                     rec->factor[lane] = wm.fac[lane];
@@ -91,7 +150,8 @@ __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOC
                     rec->hit = r.hit;
                     rec->depth = (uint8_t)(r.hit ? p.k : r.depth);
                     rec->overflow = r.overflow;
-                    for (int i = 0; i < 5; i++) rec->pad[i] = 0;
+                    rec->pad = 0;
+                    rec->sectors = sectors;
                 }
                 __syncwarp();
             }
@@ -348,6 +408,32 @@ gpm_status trace_device(gpm_graph *h, const Plan &p, uint64_t seed, uint64_t fir
                         const gpm_config *cfg, gpm_sample_record *d_out) {
     return run_block(h, p, mode_of(cfg), seed, cfg ? cfg->slot : 0, first, count, cfg, 0, d_out, nullptr);
 }
+// Mean of the records' algorithmic bytes over samples [0, count) of a run's
+// stream (seed, slot, mode as the run), for gpm_result.algo_bytes_per_sample.
+gpm_status algo_bytes_mean(gpm_graph *h, const Plan &p, int mode, uint64_t seed, uint32_t slot,
+                           const gpm_config *cfg, uint64_t count, double *out) {
+    *out = 0.0;
+    if (count == 0) return GPM_OK;
+    gpm_sample_record *d = nullptr;
+    if (cudaMalloc((void **)&d, sizeof(gpm_sample_record) * count) != cudaSuccess) {
+        set_error("algorithmic bytes: device allocation of the trace failed");
+        return GPM_ERR_OOM;
+    }
+    std::vector<gpm_sample_record> rec(count);
+    gpm_status st = run_block(h, p, mode, seed, slot, 0, count, cfg, 0, d, nullptr);
+    if (st == GPM_OK && cudaMemcpy(rec.data(), d, sizeof(gpm_sample_record) * count, cudaMemcpyDeviceToHost) !=
+                            cudaSuccess) {
+        set_error("algorithmic bytes: copy back failed");
+        st = GPM_ERR_CUDA;
+    }
+    cudaFree(d);
+    if (st != GPM_OK) return st;
+    uint64_t sec = 0;
+    for (const auto &r : rec) sec += r.sectors;
+    *out = 32.0 * (double)sec / (double)count;
+    return GPM_OK;
+}
+
 }  // namespace gpm
 
 extern "C" gpm_status gpm_sample_sums(gpm_graph *h, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
