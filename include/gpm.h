@@ -59,7 +59,14 @@ typedef enum {
 
 typedef enum {
     GPM_VERIFY_INTERSECT = 0,  /* draw from the full candidate set S_j (Algorithm 4) */
-    GPM_VERIFY_CHECK = 1       /* draw from one restricted list L_j, verify S_j membership by binary search */
+    GPM_VERIFY_CHECK = 1,      /* draw from one restricted list L_j, verify S_j membership by binary search */
+    GPM_VERIFY_LAZY = 2        /* NS-base, the lazy verify of Sec. 2.2.1 / Algorithm 1 that Sec. 4.2 prunes:
+                                  first edge from the 2m directed entries (M = 2m), x drawn from the union
+                                  U_j of the back-neighbours' lists (the first one's list whole, then each
+                                  later list's entries no earlier list holds, back-neighbours by position,
+                                  lists ascending), factor |U_j|; after the last draw the closure check
+                                  (distinct vertices, every pattern edge present, every non-edge absent when
+                                  vertex-induced, every restriction) decides hit or miss (depth = k) */
 } gpm_verify;
 
 /* gpm_load_csr flags */

@@ -546,8 +546,9 @@ uint32_t og_score(float z)
     return 1u + (uint32_t)floorf(s * 4096.0f);
 }
 
-/* One sample from its choice words r[0..k-2].  'buf' must hold max-degree
- * entries, 'buf2' too (learned mode lookahead). */
+/* One sample from its choice words r[0..k-2].  'buf' must hold OG_MAXK times
+ * (max degree + 1) entries (an NS-base union spans up to k - 1 lists), 'buf2'
+ * too (learned mode lookahead). */
 int og_sample(const og_graph *g, const og_plan *p, const uint64_t *r, int mode,
               const og_mlp *mlp, uint32_t *buf, uint32_t *buf2, og_record *rec)
 {
@@ -758,7 +759,7 @@ int og_ns_run(const og_graph *g, const og_plan *p, int mode, const og_mlp *mlp,
               uint64_t seed, uint32_t slot, uint64_t first, uint64_t count,
               og_sums *acc, og_record *recs, int want_bytes)
 {
-    uint64_t md = og_maxdeg(g) + 1;
+    uint64_t md = (og_maxdeg(g) + 1) * OG_MAXK;   /* NS-base unions span several lists */
     uint32_t *buf = (uint32_t *)malloc(sizeof(uint32_t) * md);
     uint32_t *buf2 = (uint32_t *)malloc(sizeof(uint32_t) * md);
     if (!buf || !buf2) { free(buf); free(buf2); return -1; }
@@ -784,7 +785,7 @@ int og_ns_run(const og_graph *g, const og_plan *p, int mode, const og_mlp *mlp,
 int og_ns_bytes(const og_graph *g, const og_plan *p, int mode, const og_mlp *mlp,
                 uint64_t seed, uint32_t slot, uint64_t first, uint64_t count, double *out)
 {
-    uint64_t md = og_maxdeg(g) + 1;
+    uint64_t md = (og_maxdeg(g) + 1) * OG_MAXK;   /* NS-base unions span several lists */
     uint32_t *buf = (uint32_t *)malloc(sizeof(uint32_t) * md);
     uint32_t *buf2 = (uint32_t *)malloc(sizeof(uint32_t) * md);
     if (!buf || !buf2) { free(buf); free(buf2); return -1; }

@@ -246,7 +246,7 @@ def sample(g, p, r, mode=INTERSECT, mlp=None):
     """One sample from explicit choice words r[0..k-2]."""
     L = lib()
     rr = (C.c_uint64 * MAXK)(*([int(x) for x in r] + [0] * (MAXK - len(r))))
-    md = g.max_degree + 1
+    md = (g.max_degree + 1) * MAXK      # an NS-base union spans up to k - 1 lists
     buf = np.zeros(md, dtype=np.uint32)
     buf2 = np.zeros(md, dtype=np.uint32)
     rec = Record()

@@ -22,7 +22,7 @@ GPM_ERR_ABORTED = -6
 GPM_ERR_UNSUPPORTED = -8
 
 NS, GS, HYBRID, NS_LEARNED, EXACT = 0, 1, 2, 3, 4
-VERIFY_INTERSECT, VERIFY_CHECK = 0, 1
+VERIFY_INTERSECT, VERIFY_CHECK, VERIFY_LAZY = 0, 1, 2
 DEVICE_PTRS, VALIDATE = 1, 2
 
 STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_GRAPH", -3: "ERR_OOM", -4: "ERR_CUDA",

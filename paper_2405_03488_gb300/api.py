@@ -9,7 +9,7 @@ import torch
 from . import _lib
 from . import graphs as _graphs
 from ._lib import (DEVICE_PTRS, EXACT, GS, HYBRID, NS, NS_LEARNED,  # noqa: F401
-                   VALIDATE, VERIFY_CHECK, VERIFY_INTERSECT, check, make_pattern)
+                   VALIDATE, VERIFY_CHECK, VERIFY_INTERSECT, VERIFY_LAZY, check, make_pattern)
 
 RECORD_DTYPE = np.dtype([("factor", np.uint64, _lib.MAX_K), ("w_u64", np.uint64), ("w_f64", np.float64),
                          ("vert", np.uint32, _lib.MAX_K), ("aux", np.uint32, _lib.MAX_K), ("hit", np.uint8),
@@ -42,7 +42,7 @@ def config(**kw):
         if val is None:
             continue
         if key == "verify" and isinstance(val, str):
-            val = {"intersect": VERIFY_INTERSECT, "check": VERIFY_CHECK}[val]
+            val = {"intersect": VERIFY_INTERSECT, "check": VERIFY_CHECK, "lazy": VERIFY_LAZY}[val]
         setattr(cfg, key, val)
     keep = []
     if mlp is not None:

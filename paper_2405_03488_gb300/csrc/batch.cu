@@ -311,6 +311,7 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
     uint32_t blocks = 0;
     if (e == cudaSuccess)
         e = (kmode == MODE_CHECK)     ? batch_grid<MODE_CHECK, false>(h, sh, &blocks)
+            : (kmode == MODE_LAZY)    ? batch_grid<MODE_LAZY, false>(h, sh, &blocks)
             : (kmode == MODE_LEARNED) ? batch_grid<MODE_LEARNED, false>(h, sh, &blocks)
             : (kmode == MODE_INTERSECT_SINGLE)
                 ? (compact ? batch_grid<MODE_INTERSECT_SINGLE, true>(h, sh, &blocks)
@@ -325,6 +326,9 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
             cudaEventRecordWithFlags(ev_k[2 * r], cs, cudaEventRecordExternal);
             if (kmode == MODE_CHECK)
                 ns_batch_kernel<MODE_CHECK, false>
+                    <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
+            else if (kmode == MODE_LAZY)
+                ns_batch_kernel<MODE_LAZY, false>
                     <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
             else if (kmode == MODE_LEARNED)
                 ns_batch_kernel<MODE_LEARNED, false>
@@ -450,8 +454,7 @@ extern "C" gpm_status gpm_estimate_batch(gpm_graph *h, uint32_t count, const gpm
         }
     }
     h->abort_flag = 0;
-    const int mode = (cfg && cfg->verify == GPM_VERIFY_CHECK) ? MODE_CHECK : MODE_INTERSECT;
-    return batch_estimate(h, plans, eps, delta, seed, cfg, out, mode);
+    return batch_estimate(h, plans, eps, delta, seed, cfg, out, verify_mode(cfg));
 }
 
 extern "C" gpm_status gpm_autotune(gpm_graph *h, uint32_t count, const gpm_pattern *patterns, uint64_t seed,
@@ -484,7 +487,7 @@ extern "C" gpm_status gpm_autotune(gpm_graph *h, uint32_t count, const gpm_patte
             t.window = io->window ? io->window : (1ull << 18);
             t.n_min = t.window;
             t.n_max = t.window;
-            const int mode = (t.verify == GPM_VERIFY_CHECK) ? MODE_CHECK : MODE_INTERSECT;
+            const int mode = verify_mode(&t);
             gpm_status st = batch_estimate(h, plans, eps.data(), 0.01, seed, &t, res.data(), mode);
             if (st != GPM_OK && st != GPM_ERR_NOT_CONVERGED) return st;
             if (res[0].t_sample_s < best) {

@@ -71,6 +71,21 @@ template <int MODE>
 __device__ uint32_t algo_sectors(const DGraph &g, const Plan &p, const uint32_t *v, const uint64_t *fac, int depth,
                                  bool hit) {
     uint32_t sec = 1;
+    if (MODE == MODE_LAZY) {
+        // NS-base: whole back-neighbour lists per step, one search per checked pair
+        if (depth < p.k) return sec;
+        for (int j = 2; j < p.k; j++)
+            for (int i = 0; i < j; i++)
+                if ((p.back[j] >> i) & 1u) {
+                    const uint64_t rb = __ldg(g.row_ptr + v[i]), re = __ldg(g.row_ptr + v[i] + 1);
+                    sec += 1u + (re > rb ? (uint32_t)((re * 4 + 31) / 32 - (rb * 4) / 32) : 0u);
+                }
+        for (int j = 1; j < p.k; j++)
+            for (int i = 0; i < j; i++)
+                if (((p.back[j] >> i) & 1u) || p.induced)
+                    sec += 1u + log2_ceil_plus1(__ldg(g.row_ptr + v[i] + 1) - __ldg(g.row_ptr + v[i]));
+        return sec;
+    }
     const int steps = hit ? p.k : depth + 1;
     for (int j = 2; j < steps && j < p.k; j++) {
         const uint32_t lm = p.lower[j];
@@ -136,7 +151,7 @@ __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOC
             }
             if (TRACE) {
                 __syncwarp();
-                const uint32_t sectors = algo_sectors<MODE == MODE_CHECK ? MODE_CHECK : MODE_INTERSECT>(
+                const uint32_t sectors = algo_sectors<(MODE == MODE_CHECK || MODE == MODE_LAZY) ? MODE : MODE_INTERSECT>(
                     g, p, wm.v, wm.fac, r.hit ? p.k : r.depth, r.hit);
                 gpm_sample_record *rec = a.trace + (s - a.first);
                 if (lane < kMaxK) {
@@ -241,6 +256,7 @@ static cudaError_t launch_mode(gpm_graph *h, const Plan &p, const Shape &sh, con
         case MODE_CHECK: return launch_ns<MODE_CHECK, TRACE>(h, p, sh, a);
         case MODE_LEARNED: return launch_ns<MODE_LEARNED, TRACE>(h, p, sh, a);
         case MODE_INTERSECT_SINGLE: return launch_ns<MODE_INTERSECT_SINGLE, TRACE>(h, p, sh, a);
+        case MODE_LAZY: return launch_ns<MODE_LAZY, TRACE>(h, p, sh, a);
         default: return launch_ns<MODE_INTERSECT, TRACE>(h, p, sh, a);
     }
 }
@@ -333,7 +349,7 @@ static gpm_status plan_or_error(const gpm_pattern *pat, Plan *p) {
 // gpm_sample_sums / gpm_trace: weights in cfg->mlp select the learned proposal
 static int mode_of(const gpm_config *cfg) {
     if (cfg && cfg->mlp) return MODE_LEARNED;
-    return (cfg && cfg->verify == GPM_VERIFY_CHECK) ? MODE_CHECK : MODE_INTERSECT;
+    return verify_mode(cfg);
 }
 
 // Phi^-1 by Newton iteration on the complementary error function, solved in
@@ -375,8 +391,7 @@ gpm_status ns_estimate(gpm_graph *h, const Plan &p, double eps, double delta, ui
     }
     h->abort_flag = 0;
     std::vector<Plan> plans(1, p);
-    const int mode = (cfg && cfg->verify == GPM_VERIFY_CHECK) ? MODE_CHECK : MODE_INTERSECT;
-    return batch_estimate(h, plans, &eps, delta, seed, cfg, out, mode);
+    return batch_estimate(h, plans, &eps, delta, seed, cfg, out, verify_mode(cfg));
 }
 
 // NS with the learned proposal: the same rounds, candidates drawn by score.

@@ -12,7 +12,11 @@
 
 namespace gpm {
 
-enum { MODE_INTERSECT = 0, MODE_CHECK = 1, MODE_LEARNED = 2, MODE_INTERSECT_SINGLE = 3 };
+enum { MODE_INTERSECT = 0, MODE_CHECK = 1, MODE_LEARNED = 2, MODE_INTERSECT_SINGLE = 3, MODE_LAZY = 4 };
+// MODE_LAZY is NS-base (Sec. 2.2.1, Algorithm 1; the lazy verify Sec. 4.2
+// contrasts with eager verify): x is drawn from the union U_j of the
+// back-neighbours' lists and every constraint waits for the closure check
+// after the last draw.
 // MODE_INTERSECT_SINGLE is MODE_INTERSECT compiled with the position form of
 // single-list steps (below); plans without such steps run the plain variant,
 // whose code stays as small as before.
@@ -182,17 +186,19 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
         return ((uint64_t)hi << 32) | lo;
     };
 
-    const uint64_t M = p.oriented ? g.m : g.nnz;
+    // NS-base draws from all 2m directed entries: its restrictions wait for the closure
+    const bool orient = (MODE != MODE_LAZY) && p.oriented;
+    const uint64_t M = orient ? g.m : g.nnz;
     if (lane == 0) wm.fac[0] = M;
     if (M == 0) return out;
     const uint64_t e = index_map(word(0), M);
     uint32_t v0, v1;
     uint64_t pos01 = ~0ull;  // index of v1 inside N(v0) in col, when known
-    if (p.oriented && g.edges) {
+    if (orient && g.edges) {
         const uint64_t pr = __ldg(g.edges + e);
         v0 = (uint32_t)pr;
         v1 = (uint32_t)(pr >> 32);
-    } else if (p.oriented) {
+    } else if (orient) {
         const uint64_t u = warp_upper_bound(g.uoff, g.n + 1, e) - 1;
         v0 = (uint32_t)u;
         pos01 = __ldg(g.up + u) + (e - __ldg(g.uoff + u));
@@ -248,7 +254,78 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
         uint32_t pick = 0;   // 1 + index of x in the on-chip S_j (0: not drawn from it)
         bool learned_step = false;
         double lfac = 1.0;
-        if (MODE == MODE_CHECK) {
+        if (MODE == MODE_LAZY) {
+            // U_j in list order: the first back-neighbour's list whole, then
+            // each later back-neighbour's entries that no earlier one holds
+            const uint32_t back = p.back[j];
+            auto fresh = [&](uint32_t y, int i) -> bool {
+                bool ok = true;
+                for (int q = 0; q < i; q++) {
+                    if (!((back >> q) & 1u)) continue;
+                    const uint64_t bq = __shfl_sync(kFull, lb, q);
+                    const uint64_t eq = __shfl_sync(kFull, le, q);
+                    ok = ok && !lane_contains(g.col + bq, eq - bq, y);
+                }
+                return ok;
+            };
+            uint64_t my_kept = 0;   // lane i: entries back-neighbour i adds to U_j
+            for (int i = 0; i < j; i++) {
+                if (!((back >> i) & 1u)) continue;
+                const uint64_t b = __shfl_sync(kFull, lb, i);
+                const uint64_t en = __shfl_sync(kFull, le, i);
+                uint64_t c = 0;
+                if ((back & ((1u << i) - 1u)) == 0) {
+                    c = en - b;
+                } else {
+                    for (uint64_t base = b; base < en; base += 32) {
+                        const uint64_t idx = base + lane;
+                        const bool valid = idx < en;
+                        const uint32_t y = valid ? __ldg(g.col + idx) : 0u;
+                        const bool ok = fresh(y, i) && valid;
+                        c += __popc(__ballot_sync(kFull, ok));
+                    }
+                }
+                if ((int)lane == i) my_kept = c;
+                size += c;
+            }
+            if (lane == 0) wm.fac[j] = size;
+            if (size == 0) {
+                out.depth = j;
+                return out;
+            }
+            uint64_t t = index_map(r, size);
+            for (int i = 0; i < j; i++) {
+                if (!((back >> i) & 1u)) continue;
+                const uint64_t c = __shfl_sync(kFull, my_kept, i);
+                if (t >= c) {
+                    t -= c;
+                    continue;
+                }
+                const uint64_t b = __shfl_sync(kFull, lb, i);
+                const uint64_t en = __shfl_sync(kFull, le, i);
+                if ((back & ((1u << i) - 1u)) == 0) {
+                    x = __ldg(g.col + b + t);
+                } else {
+                    uint64_t seen = 0;
+                    for (uint64_t base = b; base < en; base += 32) {
+                        const uint64_t idx = base + lane;
+                        const bool valid = idx < en;
+                        const uint32_t y = valid ? __ldg(g.col + idx) : 0u;
+                        const bool ok = fresh(y, i) && valid;
+                        const unsigned m = __ballot_sync(kFull, ok);
+                        const uint64_t cm = __popc(m);
+                        if (seen + cm > t) {
+                            const uint32_t rank = (uint32_t)(t - seen);
+                            const bool mine = ok && (uint32_t)__popc(m & lanemask_lt()) == rank;
+                            x = __shfl_sync(kFull, y, __ffs(__ballot_sync(kFull, mine)) - 1);
+                            break;
+                        }
+                        seen += cm;
+                    }
+                }
+                break;
+            }
+        } else if (MODE == MODE_CHECK) {
             const int pb = (int)p.last_back[j];
             const uint64_t b = __shfl_sync(kFull, lb, pb);
             const uint64_t en = __shfl_sync(kFull, le, pb);
@@ -561,8 +638,36 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
         }
         out.depth = j + 1;
     }
-    out.hit = true;
     out.depth = k;
+    if (MODE == MODE_LAZY) {
+        // closure check over every pair i < j: distinct, pattern edges present,
+        // pattern non-edges absent when vertex-induced, restrictions hold;
+        // pair q = j (j - 1) / 2 + i, one lane per pair
+        const int npairs = k * (k - 1) / 2;
+        bool ok = true;
+        for (int base = 0; base < npairs; base += 32) {
+            const int q = base + (int)lane;
+            const int qq = q < npairs ? q : 0;
+            int jj = 1;
+            while ((jj + 1) * jj / 2 <= qq) jj++;
+            const int ii = qq - jj * (jj - 1) / 2;
+            const uint64_t bi = __shfl_sync(kFull, lb, ii);
+            const uint64_t ei = __shfl_sync(kFull, le, ii);
+            if (q < npairs) {
+                const uint32_t vi = wm.v[ii], vj = wm.v[jj];
+                bool good = vi != vj;
+                const bool edge = (p.back[jj] >> ii) & 1u;
+                if (good && (edge || p.induced)) {
+                    const bool adj = lane_contains(g.col + bi, ei - bi, vj);
+                    good = edge ? adj : !adj;
+                }
+                if ((p.lower[jj] >> ii) & 1u) good = good && vi < vj;
+                ok = ok && good;
+            }
+        }
+        if (!__all_sync(kFull, ok)) return out;
+    }
+    out.hit = true;
     out.w = w;
     out.wu = (MODE == MODE_LEARNED || ovf) ? 0 : wu;
     out.overflow = ovf;
@@ -576,6 +681,14 @@ inline bool plan_single_steps(const Plan &p) {
     for (int j = 2; j < p.k; j++)
         if ((p.back[j] & (p.back[j] - 1u)) == 0) return true;
     return false;
+}
+
+// The uniform-proposal mode a configuration asks for.
+inline int verify_mode(const gpm_config *cfg) {
+    if (!cfg) return MODE_INTERSECT;
+    if (cfg->verify == GPM_VERIFY_CHECK) return MODE_CHECK;
+    if (cfg->verify == GPM_VERIFY_LAZY) return MODE_LAZY;
+    return MODE_INTERSECT;
 }
 
 // The sampler variant a mode runs with for a plan (or a batch of plans).
@@ -616,6 +729,7 @@ inline uint32_t fit_cap(const gpm_graph *h, size_t static_smem, uint32_t warps, 
 // searches in global memory, which want the L1 capacity a larger shared-memory
 // carve-out takes, so they keep 512 entries; otherwise fit_cap.
 inline uint32_t default_cap(const gpm_graph *h, size_t static_smem, uint32_t warps, int mode, bool induced) {
+    if (mode == MODE_LAZY) return 32;   // NS-base builds no candidate set on chip
     const uint32_t fit = fit_cap(h, static_smem, warps, mode);
     return (induced && mode != MODE_LEARNED && fit > 512) ? 512 : fit;
 }

@@ -29,14 +29,14 @@ def bytes_gpu(g, pat, seed, first, count, **cfg):
     return 32.0 * g.trace(pat, seed=seed, first=first, count=count, **cfg)["sectors"].astype(np.float64)
 
 
-@pytest.mark.parametrize("verify", ["intersect", "check"])
+@pytest.mark.parametrize("verify", ["intersect", "check", "lazy"])
 @pytest.mark.parametrize("name,induced", PATTERNS)
 def test_sectors_equal_oracle_small(name, induced, verify):
     rp, col = G.erdos_renyi(60, 0.25, seed=8)
     g = api.Graph(rp.cuda(), col.cuda())
     og = O.Graph(*G.to_numpy(rp, col))
     k, edges = G.pattern(name)
-    mode = O.CHECK if verify == "check" else O.INTERSECT
+    mode = {"intersect": O.INTERSECT, "check": O.CHECK, "lazy": O.LAZY}[verify]
     gb = bytes_gpu(g, (k, edges, induced), 21, 777, 2500, verify=verify)
     cb = O.ns_bytes(og, O.plan(k, edges, induced), seed=21, first=777, count=2500, mode=mode)
     bad = np.nonzero(gb != cb)[0]
