@@ -42,7 +42,8 @@ typedef enum {
     GPM_ERR_CUDA = -4,            /* a CUDA runtime call failed */
     GPM_ERR_NOT_CONVERGED = -5,   /* n_max or max_seconds reached; the result is filled */
     GPM_ERR_ABORTED = -6,         /* gpm_abort() was called; the result is filled */
-    GPM_ERR_UNSUPPORTED = -8      /* the combination of options is not implemented */
+    GPM_ERR_UNSUPPORTED = -8,     /* the combination of options is not implemented */
+    GPM_ERR_COMM = -9             /* the caller's gather callback reported a failure */
 } gpm_status;
 
 typedef enum {
@@ -286,6 +287,44 @@ gpm_status gpm_sample_partials(gpm_graph *g, const gpm_pattern *pattern, uint64_
  * the runs (run t += run t + h for h = 512, 256, ..., 1) -- so the result is
  * bit-identical to the device's.  n < 2^32.  Needs no GPU. */
 gpm_status gpm_merge_partials(const gpm_partial *parts, uint64_t n, gpm_sums *out);
+
+/* ---- multi-GPU rounds (Algorithm 3 with each window split over ranks) ----
+ * A window's chunk-order reduction adds 1024 contiguous runs of
+ * per = ceil(ceil(count / 64) / 1024) chunks each, left to right, then folds
+ * the runs pairwise (run t += run t + h, h = 512, 256, ..., 1).  Rank r of
+ * `world` (1 <= world <= 1024) owns the runs [r B, min((r + 1) B, 1024)),
+ * B = ceil(1024 / world): one contiguous range of samples.  Gathering every
+ * rank's B run sums in rank order and folding the first 1024 gives the
+ * one-GPU totals of the window bit for bit. */
+
+/* This rank's run sums of samples [first, first + count): out (HOST, B entries,
+ * zeros for runs past the window's chunks). */
+gpm_status gpm_sample_runs(gpm_graph *g, const gpm_pattern *pattern, uint64_t seed, uint64_t first, uint64_t count,
+                           uint32_t rank, uint32_t world, const gpm_config *cfg, gpm_partial *out);
+
+/* Host-only: the pairwise fold of 1024 run sums (HOST, in run order) into
+ * totals.  Needs no GPU. */
+gpm_status gpm_merge_runs(const gpm_partial *runs, gpm_sums *out);
+
+/* All-gather supplied by the caller (NCCL, MPI, torch.distributed, ...):
+ * every rank passes `bytes` bytes in `send` and receives all ranks' blocks,
+ * in rank order, in `recv` (world x bytes).  Returns 0 on success. */
+typedef int (*gpm_allgather_fn)(void *ctx, const void *send, void *recv, size_t bytes);
+
+/* Algorithm 3 over `world` ranks, one call per rank (each on its own GPU and
+ * handle of the same graph): every window, this rank samples its run block
+ * (gpm_sample_runs), `gather` exchanges B x 32 bytes, and every rank folds the
+ * runs and applies the window test (gpm_window_update) identically, so all
+ * ranks stop together with the one-GPU gpm_estimate's totals and estimate
+ * (same seed, cfg->slot, cfg->window) bit for bit.  cfg as for gpm_estimate
+ * (window, n_min, n_max, max_seconds, slot, verify, mlp).  state (nullable):
+ * the run's gpm_window, continued and written back, for checkpoint/resume;
+ * max_rounds > 0 stops after that many windows of this call (a paused run
+ * returns GPM_OK with state->active = 1).  GPM_ERR_COMM if the callback fails;
+ * NOT_CONVERGED / ABORTED as for gpm_estimate. */
+gpm_status gpm_estimate_sharded(gpm_graph *g, const gpm_pattern *pattern, double eps, double delta, uint64_t seed,
+                                uint32_t rank, uint32_t world, const gpm_config *cfg, gpm_allgather_fn gather,
+                                void *ctx, gpm_window *state, uint64_t max_rounds, gpm_result *out);
 
 /* Host-only: one window of Algorithm 3 (Eq. equ:error).  Folds the window's
  * totals into w (the first window is assigned, later ones added), then with

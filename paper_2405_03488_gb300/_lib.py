@@ -20,13 +20,14 @@ GPM_ERR_CUDA = -4
 GPM_ERR_NOT_CONVERGED = -5
 GPM_ERR_ABORTED = -6
 GPM_ERR_UNSUPPORTED = -8
+GPM_ERR_COMM = -9
 
 NS, GS, HYBRID, NS_LEARNED, EXACT = 0, 1, 2, 3, 4
 VERIFY_INTERSECT, VERIFY_CHECK, VERIFY_LAZY = 0, 1, 2
 DEVICE_PTRS, VALIDATE = 1, 2
 
 STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_GRAPH", -3: "ERR_OOM", -4: "ERR_CUDA",
-                -5: "ERR_NOT_CONVERGED", -6: "ERR_ABORTED", -8: "ERR_UNSUPPORTED"}
+                -5: "ERR_NOT_CONVERGED", -6: "ERR_ABORTED", -8: "ERR_UNSUPPORTED", -9: "ERR_COMM"}
 
 
 class Pattern(C.Structure):
@@ -92,6 +93,9 @@ class Window(C.Structure):
 P = C.POINTER
 _V = C.c_void_p
 _u64, _u32, _i32, _dbl = C.c_uint64, C.c_uint32, C.c_int32, C.c_double
+# int gather(void *ctx, const void *send, void *recv, size_t bytes)
+ALLGATHER_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t)
+
 SIGNATURES = [
     ("gpm_load_csr", _i32, [_u64, _V, _V, _u32, _V, P(_V)]),
     ("gpm_free_graph", None, [_V]),
@@ -106,6 +110,10 @@ SIGNATURES = [
     ("gpm_sample_partials", _i32, [_V, P(Pattern), _u64, _u64, _u64, _u32, _u32, P(Config), _V, P(_u64)]),
     ("gpm_merge_partials", _i32, [_V, _u64, P(Sums)]),
     ("gpm_window_update", _i32, [P(Window), P(Sums), _dbl, _dbl, _u64, _u64]),
+    ("gpm_sample_runs", _i32, [_V, P(Pattern), _u64, _u64, _u64, _u32, _u32, P(Config), _V]),
+    ("gpm_merge_runs", _i32, [_V, P(Sums)]),
+    ("gpm_estimate_sharded", _i32, [_V, P(Pattern), _dbl, _dbl, _u64, _u32, _u32, P(Config), _V, _V,
+                                    P(Window), _u64, P(Result)]),
     ("gpm_trace", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), _V]),
     ("gpm_exact_count", _i32, [_V, P(Pattern), P(_u64)]),
     ("gpm_mlp_scores", _i32, [_V, P(MLP), _V, _u64, _V]),

@@ -166,6 +166,52 @@ class Graph:
         assert n.value == mine
         return out[:mine]
 
+    def sample_runs(self, pat, seed, first, count, rank=0, world=1, **cfg):
+        """This rank's B = ceil(1024 / world) run sums of samples [first, first +
+        count) (a structured array with fields sum, sumsq, hits, n)."""
+        B = (1024 + world - 1) // world
+        out = np.zeros(B, dtype=PARTIAL_DTYPE)
+        pp = pattern(pat)
+        c = config(**cfg)
+        check(_lib.load().gpm_sample_runs(self.h, C.byref(pp), seed, first, count, rank, world, C.byref(c),
+                                          C.c_void_p(out.ctypes.data)), "gpm_sample_runs")
+        return out
+
+    def estimate_sharded(self, pat, rank, world, gather, eps=0.01, delta=0.01, seed=1, state=None, max_rounds=0,
+                         **cfg):
+        """gpm_estimate_sharded: this rank's part of an estimate over `world`
+        ranks.  gather(block) receives this rank's bytes (numpy uint8) and
+        returns all ranks' blocks concatenated in rank order.  state: a
+        _lib.Window to continue (written back) or None."""
+        res = _lib.Result()
+        pp = pattern(pat)
+        c = config(**cfg)
+        err = []
+
+        def cb(ctx, send, recv, nbytes):
+            try:
+                blk = np.ctypeslib.as_array(C.cast(send, C.POINTER(C.c_uint8)), shape=(nbytes,)).copy()
+                allb = np.ascontiguousarray(gather(blk), dtype=np.uint8)
+                if allb.size != nbytes * world:
+                    raise ValueError("gather returned %d bytes, expected %d" % (allb.size, nbytes * world))
+                C.memmove(recv, allb.ctypes.data, allb.size)
+                return 0
+            except Exception as e:  # reported to the library as a failed collective
+                err.append(e)
+                return 1
+
+        fn = _lib.ALLGATHER_FN(cb)
+        code = _lib.load().gpm_estimate_sharded(self.h, C.byref(pp), eps, delta, seed, rank, world, C.byref(c),
+                                                C.cast(fn, C.c_void_p), None,
+                                                C.byref(state) if state is not None else None, max_rounds,
+                                                C.byref(res))
+        if err:
+            raise err[0]
+        check(code, "gpm_estimate_sharded", (_lib.GPM_OK, _lib.GPM_ERR_NOT_CONVERGED, _lib.GPM_ERR_ABORTED))
+        d = res.as_dict()
+        d["status"] = code
+        return d
+
     def trace(self, pat, seed, first, count, **cfg):
         recs = np.zeros(count, dtype=RECORD_DTYPE)
         pp = pattern(pat)

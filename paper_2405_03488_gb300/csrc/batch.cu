@@ -55,7 +55,7 @@ template <int MODE, bool COMPACT>
 __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOCKS)
     ns_batch_kernel(const DGraph g, const Plan *__restrict__ plans, const BatchJob *jobs, BatchCtl *ctl,
                     const BatchArgs ba, Partial *partials) {
-    extern __shared__ uint64_t smem64[];
+    extern __shared__ __align__(16) uint64_t smem64[];
     __shared__ StepPlan splan[8];
     const unsigned lane = lane_id();
     WarpMem wm = warp_mem<MODE>(smem64, ba.cap, ba.mlp);

@@ -17,38 +17,45 @@ __device__ __forceinline__ float flog2p1(uint64_t d) {
     return __fadd_rn(__int2float_rn(e), frac);
 }
 
-// Score of one candidate: the 3 -> 64 -> 64 -> 1 ReLU MLP with FP32 FMA chains
-// in input order (lane l owns hidden units l and l + 32), the output mapped
-// without exp to s = clamp(z / 8 + 1/2, 0, 1) and a = 1 + floor(4096 s).
-__device__ __forceinline__ uint32_t mlp_score(const WarpMem &wm, float f0, float f1, float f2) {
-    const unsigned lane = lane_id();
-    const float *w1 = wm.W, *b1 = wm.W + 192, *w2t = wm.W + 256, *b2 = wm.W + 4352, *w3 = wm.W + 4416,
-                *b3 = wm.W + 4480;
-    float *h1 = wm.hbuf, *h2 = wm.hbuf + 64;
+// Score of one candidate, computed by one lane alone: the 3 -> 64 -> 64 -> 1
+// ReLU MLP with FP32 fused multiply-adds in input order (hidden layer 2 and
+// the output chain walk the units in ascending order, as the oracle does),
+// weights read as broadcasts from the block's copy (W2 row-major, rows of 64
+// loaded 4 at a time), the output mapped without exp to
+// s = clamp(z / 8 + 1/2, 0, 1) and a = 1 + floor(4096 s).
+__device__ __forceinline__ uint32_t mlp_score_lane(const float *W, float f0, float f1, float f2) {
+    const float *w1 = W, *b1 = W + 192, *w2 = W + 256, *b2 = W + 4352, *w3 = W + 4416, *b3 = W + 4480;
+    float h1[64];
 #pragma unroll
-    for (int hh = 0; hh < 2; hh++) {
-        const int o = lane + 32 * hh;
+    for (int o = 0; o < 64; o++) {
         float acc = b1[o];
         acc = __fmaf_rn(w1[o * 3 + 0], f0, acc);
         acc = __fmaf_rn(w1[o * 3 + 1], f1, acc);
         acc = __fmaf_rn(w1[o * 3 + 2], f2, acc);
         h1[o] = acc > 0.f ? acc : 0.f;
     }
-    __syncwarp();
-    float r2[2];
-#pragma unroll
-    for (int hh = 0; hh < 2; hh++) {
-        const int o = lane + 32 * hh;
-        float acc = b2[o];
-        for (int i = 0; i < 64; i++) acc = __fmaf_rn(w2t[i * 64 + o], h1[i], acc);
-        r2[hh] = acc > 0.f ? acc : 0.f;
-    }
-    h2[lane] = r2[0];
-    h2[lane + 32] = r2[1];
-    __syncwarp();
     float z = b3[0];
-    for (int i = 0; i < 64; i++) z = __fmaf_rn(w3[i], h2[i], z);
-    __syncwarp();
+#pragma unroll 1
+    for (int o = 0; o < 64; o += 2) {
+        // two hidden units at a time: two independent chains, each in input order
+        const float4 *ra = reinterpret_cast<const float4 *>(w2 + o * 64);
+        const float4 *rb = reinterpret_cast<const float4 *>(w2 + (o + 1) * 64);
+        float acc_a = b2[o], acc_b = b2[o + 1];
+#pragma unroll
+        for (int i4 = 0; i4 < 16; i4++) {
+            const float4 wa = ra[i4], wb = rb[i4];
+            acc_a = __fmaf_rn(wa.x, h1[4 * i4 + 0], acc_a);
+            acc_b = __fmaf_rn(wb.x, h1[4 * i4 + 0], acc_b);
+            acc_a = __fmaf_rn(wa.y, h1[4 * i4 + 1], acc_a);
+            acc_b = __fmaf_rn(wb.y, h1[4 * i4 + 1], acc_b);
+            acc_a = __fmaf_rn(wa.z, h1[4 * i4 + 2], acc_a);
+            acc_b = __fmaf_rn(wb.z, h1[4 * i4 + 2], acc_b);
+            acc_a = __fmaf_rn(wa.w, h1[4 * i4 + 3], acc_a);
+            acc_b = __fmaf_rn(wb.w, h1[4 * i4 + 3], acc_b);
+        }
+        z = __fmaf_rn(w3[o], acc_a > 0.f ? acc_a : 0.f, z);
+        z = __fmaf_rn(w3[o + 1], acc_b > 0.f ? acc_b : 0.f, z);
+    }
     float sc = __fmaf_rn(z, 0.125f, 0.5f);
     if (!(sc > 0.f)) sc = 0.f;
     if (sc > 1.f) sc = 1.f;
@@ -152,12 +159,26 @@ static __device__ __noinline__ uint32_t learned_pick(const DGraph &g, const Plan
         cu[i] = (uint32_t)(__ldg(g.up + x) - xb);
     }
     __syncwarp();
-    uint64_t A = 0;
+    // lookahead sizes |S_{j+1}(x)|, one warp-wide count per candidate, into cu
     for (uint32_t i = 0; i < sz; i++) {
         const uint64_t xb = cb[i], dx = cd[i];
         const uint64_t nxt = lookahead_count(g, p, wm, Sj, sz, i, j, lb, le, xb, xb + dx, xb + cu[i]);
-        const uint32_t a = mlp_score(wm, flog2p1(dx), __int2float_rn(j), flog2p1(nxt));
-        if (lane == 0) wm.score[i] = a;
+        __syncwarp();
+        if (lane == 0) cu[i] = (uint32_t)nxt;
+    }
+    __syncwarp();
+    // scores, one candidate per lane
+    uint64_t A = 0;
+    const float fj = __int2float_rn(j);
+    for (uint32_t base = 0; base < sz; base += 32) {
+        const uint32_t i = base + lane;
+        uint32_t a = 0;
+        if (i < sz) {
+            a = mlp_score_lane(wm.W, flog2p1(cd[i]), fj, flog2p1(cu[i]));
+            wm.score[i] = a;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
         A += a;
     }
     __syncwarp();

@@ -38,14 +38,12 @@ constexpr int kW1 = 0, kB1 = 192, kW2 = 256, kB2 = 4352, kW3 = 4416, kB3 = 4480;
 // ------------------------------------------------------------------ scoring
 __global__ void __launch_bounds__(256) mlp_score_kernel(const gpm_mlp mlp, const float *__restrict__ feat,
                                                         uint64_t n, uint32_t *out) {
-    extern __shared__ uint64_t smem64[];
+    extern __shared__ __align__(16) uint64_t smem64[];
     WarpMem wm = warp_mem<MODE_LEARNED>(smem64, 0, mlp);
-    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t r = warp; r < n; r += nw) {
-        const uint32_t a = mlp_score(wm, feat[3 * r], feat[3 * r + 1], feat[3 * r + 2]);
-        if (lane_id() == 0) out[r] = a;
-    }
+    const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    // one row per thread (the sampler scores one candidate per lane the same way)
+    for (uint64_t r = t0; r < n; r += nt) out[r] = mlp_score_lane(wm.W, feat[3 * r], feat[3 * r + 1], feat[3 * r + 2]);
 }
 
 // ------------------------------------------------------------------ features

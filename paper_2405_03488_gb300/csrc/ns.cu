@@ -124,7 +124,7 @@ __device__ uint32_t algo_sectors(const DGraph &g, const Plan &p, const uint32_t 
 
 template <int MODE, bool TRACE>
 __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOCKS) ns_kernel(const DGraph g, const Plan p, const RunArgs a) {
-    extern __shared__ uint64_t smem64[];
+    extern __shared__ __align__(16) uint64_t smem64[];
     const unsigned lane = lane_id();
     WarpMem wm = warp_mem<MODE>(smem64, a.cap, a.mlp);
     const uint64_t end = a.first + a.count;
@@ -499,6 +499,200 @@ extern "C" gpm_status gpm_sample_partials(gpm_graph *h, const gpm_pattern *patte
     }
     *n_out = n;
     return GPM_OK;
+}
+
+// ------------------------------------------------------------------ run blocks (multi-GPU rounds)
+// The chunk-order reduction of a round (reduce_partials) adds 1024 contiguous
+// runs of ceil(nchunks / 1024) chunks left to right and then folds the runs
+// pairwise.  Rank r of `world` takes the runs [r B, (r + 1) B), B =
+// ceil(1024 / world): one contiguous range of chunks, hence of samples, whose
+// run sums it computes on its GPU exactly as the single-GPU reduction would.
+namespace gpm {
+
+constexpr uint32_t kRuns = 1024;
+
+// Run sums of a rank's chunks: run t adds partials [t per, min((t + 1) per, n))
+// left to right (one thread per run).
+__global__ void reduce_runs(const Partial *__restrict__ parts, uint32_t n, uint32_t per, uint32_t nruns,
+                            Partial *out) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nruns) return;
+    const uint64_t b = (uint64_t)t * per;
+    const uint64_t e = (b + per < n) ? b + per : n;
+    Partial q;
+    q.sum = 0.0;
+    q.sumsq = 0.0;
+    q.hits = 0;
+    q.n = 0;
+    for (uint64_t i = b; i < e; i++) {
+        q.sum = __dadd_rn(q.sum, parts[i].sum);
+        q.sumsq = __dadd_rn(q.sumsq, parts[i].sumsq);
+        q.hits += parts[i].hits;
+        q.n += parts[i].n;
+    }
+    out[t] = q;
+}
+
+// This rank's run sums of samples [first, first + count) into host out[B].
+static gpm_status sample_runs(gpm_graph *h, const Plan &p, int mode, uint64_t seed, uint32_t slot, uint64_t first,
+                              uint64_t count, uint32_t rank, uint32_t world, const gpm_config *cfg, gpm_partial *out) {
+    const uint32_t B = (kRuns + world - 1) / world;
+    std::memset(out, 0, sizeof(gpm_partial) * B);
+    const uint64_t nch = (count + kChunk - 1) / kChunk;
+    const uint64_t per = (nch + kRuns - 1) / kRuns;
+    const uint64_t run_lo = (uint64_t)rank * B;
+    const uint64_t run_hi = std::min<uint64_t>(run_lo + B, kRuns);
+    const uint64_t c_lo = std::min<uint64_t>(run_lo * per, nch), c_hi = std::min<uint64_t>(run_hi * per, nch);
+    if (run_lo >= run_hi || c_lo >= c_hi) return GPM_OK;
+    const uint64_t s_lo = c_lo * kChunk, s_hi = std::min<uint64_t>(c_hi * kChunk, count);
+    const uint64_t nloc = c_hi - c_lo;
+    const uint32_t nruns = (uint32_t)(run_hi - run_lo);
+    // room for the chunk partials and, after them, the run sums (before sampling:
+    // growing the array later would drop the partials)
+    gpm_status st = ensure_partials(h, nloc + nruns);
+    if (st != GPM_OK) return st;
+    st = run_block(h, p, mode, seed, slot, first + s_lo, s_hi - s_lo, cfg, 0, nullptr, nullptr);
+    if (st != GPM_OK) return st;
+    Partial *d_runs = h->partials + nloc;
+    reduce_runs<<<(nruns + 127) / 128, 128, 0, h->stream>>>(h->partials, (uint32_t)nloc, (uint32_t)per, nruns,
+                                                            d_runs);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_runs, sizeof(Partial) * nruns, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("run sums: ") + cudaGetErrorString(e));
+        return GPM_ERR_CUDA;
+    }
+    return GPM_OK;
+}
+
+// The pairwise tree over 1024 run sums (the second half of reduce_partials).
+static void merge_runs(const gpm_partial *runs, gpm_sums *out) {
+    std::vector<double> s_sum(kRuns), s_sq(kRuns);
+    std::vector<uint64_t> s_hits(kRuns), s_n(kRuns);
+    for (uint32_t t = 0; t < kRuns; t++) {
+        s_sum[t] = runs[t].sum;
+        s_sq[t] = runs[t].sumsq;
+        s_hits[t] = runs[t].hits;
+        s_n[t] = runs[t].n;
+    }
+    for (uint32_t hh = kRuns / 2; hh; hh >>= 1)
+        for (uint32_t t = 0; t < hh; t++) {
+            s_sum[t] = rn_add(s_sum[t], s_sum[t + hh]);
+            s_sq[t] = rn_add(s_sq[t], s_sq[t + hh]);
+            s_hits[t] += s_hits[t + hh];
+            s_n[t] += s_n[t + hh];
+        }
+    out->n = s_n[0];
+    out->hits = s_hits[0];
+    out->sum = s_sum[0];
+    out->sumsq = s_sq[0];
+}
+
+}  // namespace gpm
+
+extern "C" gpm_status gpm_sample_runs(gpm_graph *h, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
+                                      uint64_t count, uint32_t rank, uint32_t world, const gpm_config *cfg,
+                                      gpm_partial *out) {
+    if (!h || !out || world == 0 || world > kRuns || rank >= world) {
+        set_error("gpm_sample_runs: null argument, world outside 1..1024 or rank >= world");
+        return GPM_ERR_ARG;
+    }
+    Plan p;
+    gpm_status st = plan_or_error(pattern, &p);
+    if (st != GPM_OK) return st;
+    return sample_runs(h, p, mode_of(cfg), seed, cfg ? cfg->slot : 0, first, count, rank, world, cfg, out);
+}
+
+extern "C" gpm_status gpm_merge_runs(const gpm_partial *runs, gpm_sums *out) {
+    if (!runs || !out) {
+        set_error("gpm_merge_runs: null argument");
+        return GPM_ERR_ARG;
+    }
+    merge_runs(runs, out);
+    return GPM_OK;
+}
+
+extern "C" gpm_status gpm_estimate_sharded(gpm_graph *h, const gpm_pattern *pattern, double eps, double delta,
+                                           uint64_t seed, uint32_t rank, uint32_t world, const gpm_config *cfg,
+                                           gpm_allgather_fn gather, void *ctx, gpm_window *state,
+                                           uint64_t max_rounds, gpm_result *out) {
+    if (!h || !out || !gather || world == 0 || world > kRuns || rank >= world) {
+        set_error("gpm_estimate_sharded: null argument, world outside 1..1024 or rank >= world");
+        return GPM_ERR_ARG;
+    }
+    if (!(eps > 0.0) || !(delta > 0.0 && delta < 1.0)) {
+        set_error("eps must be > 0 and delta in (0, 1)");
+        return GPM_ERR_ARG;
+    }
+    std::memset(out, 0, sizeof(*out));
+    Plan p;
+    gpm_status st = plan_or_error(pattern, &p);
+    if (st != GPM_OK) return st;
+    const auto t0 = std::chrono::steady_clock::now();
+    const uint64_t W = (cfg && cfg->window) ? cfg->window : (1ull << 20);
+    const uint64_t n_min = (cfg && cfg->n_min) ? cfg->n_min : W;
+    const uint64_t n_max = (cfg && cfg->n_max) ? cfg->n_max : (1ull << 40);
+    const double max_s = cfg ? cfg->max_seconds : 0.0;
+    const double z = normal_quantile(1.0 - delta / 2.0);
+    const int mode = mode_of(cfg);
+    const uint32_t B = (kRuns + world - 1) / world;
+    gpm_window w;
+    if (state) {
+        w = *state;
+    } else {
+        std::memset(&w, 0, sizeof(w));
+        w.active = 1;
+    }
+    std::vector<gpm_partial> mine(B), all((size_t)B * world);
+    h->abort_flag = 0;
+    uint64_t done = 0, launches = 0;
+    double t_sample = 0.0;
+    while (w.active && (max_rounds == 0 || done < max_rounds)) {
+        const auto ta = std::chrono::steady_clock::now();
+        st = sample_runs(h, p, mode, seed, cfg ? cfg->slot : 0, w.rounds * W, W, rank, world, cfg, mine.data());
+        if (st != GPM_OK) return st;
+        t_sample += std::chrono::duration<double>(std::chrono::steady_clock::now() - ta).count();
+        launches += 3;
+        if (gather(ctx, mine.data(), all.data(), sizeof(gpm_partial) * B) != 0) {
+            set_error("gpm_estimate_sharded: the gather callback failed");
+            return GPM_ERR_COMM;
+        }
+        gpm_sums win;
+        merge_runs(all.data(), &win);
+        gpm_window_update(&w, &win, z, eps, n_min, n_max);
+        done++;
+        if (h->abort_flag) {
+            st = GPM_ERR_ABORTED;
+            set_error("aborted");
+            break;
+        }
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (w.active && max_s > 0.0 && el >= max_s) {
+            st = GPM_ERR_NOT_CONVERGED;
+            set_error("max_seconds reached before eps_hat <= eps");
+            break;
+        }
+    }
+    if (state) *state = w;
+    out->estimate = w.mu;
+    out->ci_half_width = w.half;
+    out->eps_hat = w.eps_hat;
+    out->sum = w.sum;
+    out->sumsq = w.sumsq;
+    out->samples = w.n;
+    out->hits = w.hits;
+    out->rounds = w.rounds;
+    out->scheme_used = (mode == MODE_LEARNED) ? GPM_NS_LEARNED : GPM_NS;
+    out->converged = (int32_t)w.converged;
+    out->t_sample_s = t_sample;
+    out->kernel_launches = launches;
+    out->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (st == GPM_OK && !w.converged && !w.active) {
+        st = GPM_ERR_NOT_CONVERGED;
+        set_error("n_max reached before eps_hat <= eps");
+    }
+    return st;
 }
 
 extern "C" gpm_status gpm_merge_partials(const gpm_partial *parts, uint64_t n, gpm_sums *out) {

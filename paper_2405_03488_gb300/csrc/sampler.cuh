@@ -94,8 +94,8 @@ struct WarpMem {
     const float *W;        // learned: block copy of the weights (W2 transposed)
 };
 
-// Block-level setup: the learned weights (BF16 -> FP32, W2 stored transposed
-// so lanes reading one input column hit distinct banks) and each warp's slices.
+// Block-level setup: the learned weights (BF16 -> FP32, in the gpm_mlp order;
+// every lane reads the same weight at once, a broadcast) and each warp's slices.
 template <int MODE>
 __device__ __forceinline__ WarpMem warp_mem(uint64_t *smem64, uint32_t cap, const gpm_mlp &mlp) {
     uint32_t *smem = reinterpret_cast<uint32_t *>(smem64);
@@ -105,10 +105,8 @@ __device__ __forceinline__ WarpMem warp_mem(uint64_t *smem64, uint32_t cap, cons
         for (int i = threadIdx.x; i < kMlpFloats; i += blockDim.x) {
             if (i < 192) W[i] = bf(mlp.w1, i);
             else if (i < 256) W[i] = bf(mlp.b1, i - 192);
-            else if (i < 4352) {
-                const int t = i - 256, o = t >> 6, in = t & 63;
-                W[256 + in * 64 + o] = bf(mlp.w2, t);
-            } else if (i < 4416) W[i] = bf(mlp.b2, i - 4352);
+            else if (i < 4352) W[i] = bf(mlp.w2, i - 256);
+            else if (i < 4416) W[i] = bf(mlp.b2, i - 4352);
             else if (i < 4480) W[i] = bf(mlp.w3, i - 4416);
             else W[i] = bf(mlp.b3, 0);
         }
@@ -494,6 +492,33 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                     }
                     return ok;
                 };
+                // the same conditions gathered once per step for edge-induced
+                // plans: y must lie in the non-driver back-neighbour lists (the
+                // staged one and at most one in global memory) and differ from
+                // the earlier vertices not below the bound it already exceeds
+                // (membership in N(v_i) rules out y = v_i, the graph having no
+                // loops); pred covers every other case
+                uint32_t gmask = 0, nmask = 0;
+                if (kCompact) {
+                    for (int i = 0; i < j; i++) {
+                        const bool edge = (back >> i) & 1u;
+                        if (edge && i != driver && i != staged) gmask |= 1u << i;
+                        if (!edge && !(has_lo && wm.v[i] <= lo)) nmask |= 1u << i;
+                    }
+                }
+                const bool fast = kCompact && !p.induced && __popc(gmask) <= 1 && __popc(nmask) <= 1;
+                const int gi = gmask ? __ffs(gmask) - 1 : 0;
+                const uint64_t fb = __shfl_sync(kFull, lb, gi);
+                const uint32_t *const fptr = g.col + fb;
+                const uint32_t flen = gmask ? (uint32_t)(__shfl_sync(kFull, le, gi) - fb) : 0u;
+                if (gmask && flen == 0) empty = true;   // S_j lies inside that list
+                const uint32_t nv = nmask ? wm.v[__ffs(nmask) - 1] : 0xFFFFFFFFu;   // no vertex has this id
+                auto fast_pred = [&](uint32_t y) -> bool {
+                    bool ok = y != nv;
+                    if (staged >= 0) ok = ok && lane_contains_shared(Sp, plen, y);
+                    if (flen) ok = ok && lane_contains(fptr, flen, y);
+                    return ok;
+                };
                 if (!empty) {
                     for (uint64_t base = dstart; base < de; base += 128) {
                         uint32_t y[4];
@@ -508,7 +533,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                         for (int u = 0; u < 4; u++) {
                             if (base + 32 * u >= de) break;
                             const uint32_t yu = u == 0 ? y[0] : u == 1 ? y[1] : u == 2 ? y[2] : y[3];
-                            const bool ok = pred(yu) && (base + 32 * u + lane < de);
+                            const bool ok = (fast ? fast_pred(yu) : pred(yu)) && (base + 32 * u + lane < de);
                             const unsigned m = __ballot_sync(kFull, ok);
                             if (ok) {
                                 const uint64_t pos = count + __popc(m & lanemask_lt());
@@ -548,7 +573,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                                 for (int u = 0; u < 4; u++) {
                                     if (found || base + 32 * u >= de) break;
                                     const uint32_t yu = u == 0 ? y[0] : u == 1 ? y[1] : u == 2 ? y[2] : y[3];
-                                    const bool ok = pred(yu) && (base + 32 * u + lane < de);
+                                    const bool ok = (fast ? fast_pred(yu) : pred(yu)) && (base + 32 * u + lane < de);
                                     const unsigned m = __ballot_sync(kFull, ok);
                                     const uint64_t c = __popc(m);
                                     if (seen + c > target) {

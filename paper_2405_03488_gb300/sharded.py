@@ -1,14 +1,21 @@
 """Sharded rounds of Algorithm 3 over several ranks (one process per GPU).
 
-Within every window the 64-sample chunks are dealt round robin (chunk c to
-rank c mod world); each rank draws its chunks with ``Graph.sample_partials``,
-the ranks' partial arrays are gathered, interleaved back into chunk order and
-merged with the device's fixed-order reduction (``gpm_merge_partials``), and
-the window test runs on every rank with the same single-rounding FP64 steps
-as the device (``gpm_window_update``).  Totals, the stop window and the
-estimate are therefore bit-identical to a one-GPU ``gpm_estimate`` with the
-same seed, slot and window.  The only exchange is one gather of
-32 bytes per chunk per window.
+A window's chunk-order reduction adds 1024 contiguous runs of chunks left to
+right and then folds the runs pairwise.  Rank r of ``world`` takes the runs
+[r B, (r + 1) B), B = ceil(1024 / world): one contiguous block of samples.
+Each rank samples its block and reduces it to run sums on its GPU
+(``Graph.sample_runs``); one all-gather of B x 32 bytes per window gives every
+rank all 1024 run sums, which it folds (``gpm_merge_runs``) and feeds to the
+window test (``gpm_window_update``, the device's single-rounding FP64 steps).
+Totals, the stop window and the estimate are therefore bit-identical to a
+one-GPU ``gpm_estimate`` with the same seed, slot and window.
+
+``Graph.estimate_sharded`` runs that loop inside libgpm
+(``gpm_estimate_sharded``) with the all-gather supplied as a callback;
+``estimate_sharded`` below is the same loop in Python over any source of run
+sums (the tests feed it the CPU oracle's).  The older round-robin chunk
+deal (``Graph.sample_partials``, ``interleave``, ``merge_partials``) stays
+available.
 """
 import ctypes as C
 
@@ -35,6 +42,63 @@ def merge_partials(parts):
     check(_lib.load().gpm_merge_partials(C.c_void_p(parts.ctypes.data), len(parts), C.byref(out)),
           "gpm_merge_partials")
     return out
+
+
+RUNS = 1024
+
+
+def run_block(world):
+    """Runs per rank, B = ceil(1024 / world)."""
+    return (RUNS + world - 1) // world
+
+
+def merge_runs(runs):
+    """Totals of the first 1024 run sums (in run order), folded pairwise as
+    the device does; bit-identical to the one-GPU reduction of the window."""
+    runs = np.ascontiguousarray(runs[:RUNS])
+    if len(runs) < RUNS:
+        pad = np.zeros(RUNS, dtype=runs.dtype)
+        pad[:len(runs)] = runs
+        runs = pad
+    out = _lib.Sums()
+    check(_lib.load().gpm_merge_runs(C.c_void_p(runs.ctypes.data), C.byref(out)), "gpm_merge_runs")
+    return out
+
+
+def runs_from_partials(parts, count, rank, world):
+    """The run sums rank `rank` computes from its chunks' partials (chunk
+    order, the rank's block only): run t adds chunks [t per, (t + 1) per)
+    left to right.  Host mirror of the device's reduce_runs, for sources of
+    chunk partials other than the GPU (the CPU oracle in the tests)."""
+    nch = (count + 63) // 64
+    per = (nch + RUNS - 1) // RUNS
+    B = run_block(world)
+    out = np.zeros(B, dtype=parts.dtype)
+    lo = rank * B
+    for t in range(B):
+        g = lo + t
+        if g >= RUNS:
+            break
+        a, b = g * per - lo * per, min((g + 1) * per, nch) - lo * per
+        acc_s = acc_q = 0.0
+        hits = n = 0
+        for i in range(max(a, 0), max(b, 0)):
+            acc_s += float(parts["sum"][i])
+            acc_q += float(parts["sumsq"][i])
+            hits += int(parts["hits"][i])
+            n += int(parts["n"][i])
+        out[t] = (acc_s, acc_q, hits, n)
+    return out
+
+
+def rank_samples(count, rank, world):
+    """The contiguous sample range [lo, hi) of rank's run block in a window of count."""
+    nch = (count + 63) // 64
+    per = (nch + RUNS - 1) // RUNS
+    B = run_block(world)
+    c_lo = min(rank * B * per, nch)
+    c_hi = min(min((rank + 1) * B, RUNS) * per, nch)
+    return min(64 * c_lo, count), min(64 * c_hi, count)
 
 
 def window_update(state, sums, z, eps, n_min, n_max):
@@ -65,15 +129,15 @@ def torch_gather(group=None):
     return gather
 
 
-def estimate_sharded(partials_fn, eps, delta, window, rank, world, gather, n_min=None, n_max=1 << 40, state=None,
+def estimate_sharded(runs_fn, eps, delta, window, rank, world, gather, n_min=None, n_max=1 << 40, state=None,
                      max_rounds=None):
-    """Algorithm 3 with each window's chunks split over ``world`` ranks.
+    """Algorithm 3 with each window split over ``world`` ranks by run blocks.
 
-    partials_fn(first, count, rank, world) returns this rank's chunk partials
-    of samples [first, first + count) (``Graph.sample_partials`` with the
-    pattern, seed and slot bound); gather(local) returns every rank's array in
-    rank order.  Returns the fields of a one-GPU estimate and, under "state",
-    the running window state.
+    runs_fn(first, count, rank, world) returns this rank's B run sums of
+    samples [first, first + count) (``Graph.sample_runs`` with the pattern,
+    seed and slot bound); gather(local) returns every rank's array in rank
+    order.  Returns the fields of a one-GPU estimate and, under "state", the
+    running window state.
 
     Checkpoint and resume: ``max_rounds`` stops after that many windows of
     this call; the returned state (a ``gpm_window``, 72 bytes, ``bytes(state)``
@@ -93,8 +157,8 @@ def estimate_sharded(partials_fn, eps, delta, window, rank, world, gather, n_min
     done = 0
     while st.active and (max_rounds is None or done < max_rounds):
         first = st.rounds * window
-        local = partials_fn(first, window, rank, world)
-        merged = merge_partials(interleave(gather(local)))
+        local = runs_fn(first, window, rank, world)
+        merged = merge_runs(np.concatenate(gather(local)))
         window_update(st, merged, z, eps, n_min, n_max)
         done += 1
     return {"estimate": st.mu, "ci_half_width": st.half, "eps_hat": st.eps_hat, "samples": st.n,
@@ -122,3 +186,21 @@ def gs_estimate_sharded(count_fn, colors, k, rank, world, allreduce):
     the integers; the estimate is the total times colors^(k-1)."""
     total = allreduce(count_fn(rank, world))
     return {"exact_count": total, "estimate": float(total) * float(colors) ** (k - 1)}
+
+
+def torch_allgather_bytes(group=None):
+    """Fixed-size all-gather of byte blocks over torch.distributed (gloo or
+    NCCL), for ``Graph.estimate_sharded``: gather(block) returns the ranks'
+    blocks concatenated in rank order."""
+    import torch
+    import torch.distributed as dist
+
+    def gather(block):
+        world = dist.get_world_size(group)
+        dev = torch.device("cuda") if dist.get_backend(group) == "nccl" else torch.device("cpu")
+        t = torch.from_numpy(block).to(dev)
+        outs = [torch.empty_like(t) for _ in range(world)]
+        dist.all_gather(outs, t, group=group)
+        return torch.cat(outs).cpu().numpy()
+
+    return gather

@@ -1,7 +1,8 @@
-"""Host logic of sharded rounds (Algorithm 3 with each window's chunks split
-over ranks): the chunk-order merge is the device's fixed-shape reduction; the
-window test follows Eq. equ:error step by step; two gloo ranks that deal each
-window's chunks round robin reproduce the oracle's one-process online run."""
+"""Host logic of sharded rounds (Algorithm 3 with each window split over
+ranks): the chunk-order merge is the device's fixed-shape reduction, and so is
+the fold of run sums that ranks owning contiguous run blocks produce; the
+window test follows Eq. equ:error step by step; two gloo ranks that each take
+a block of every window reproduce the oracle's one-process online run."""
 import math
 import os
 import socket
@@ -60,6 +61,31 @@ def test_merge_is_the_fixed_shape_reduction(n):
     exact = math.fsum(p["sum"].tolist())
     assert s.sum == pytest.approx(exact, rel=1e-12, abs=0.0)
     assert s.sumsq == pytest.approx(math.fsum(p["sumsq"].tolist()), rel=1e-12, abs=0.0)
+
+
+@pytest.mark.parametrize("n", [1, 63, 1024, 1025, 5000, 16384])
+def test_run_blocks_fold_to_the_chunk_order_reduction(n):
+    """Every world size: the ranks' run sums, concatenated in rank order and
+    folded, equal the chunk-order reduction of all partials bit for bit."""
+    p = random_partials(n, seed=n + 7)
+    ref = sharded.merge_partials(p)
+    count = 64 * n
+    for world in (1, 2, 3, 5, 8, 1000, 1024):
+        runs = []
+        for r in range(world):
+            lo, hi = sharded.rank_samples(count, r, world)
+            runs.append(sharded.runs_from_partials(p[lo // 64:(hi + 63) // 64], count, r, world))
+        got = sharded.merge_runs(np.concatenate(runs))
+        assert (got.n, got.hits, got.sum, got.sumsq) == (ref.n, ref.hits, ref.sum, ref.sumsq), world
+
+
+def test_rank_blocks_tile_the_window():
+    for count in (1, 64, 65, 1 << 20, 3_000_017):
+        for world in (1, 2, 3, 7, 8, 1024):
+            spans = [sharded.rank_samples(count, r, world) for r in range(world)]
+            assert spans[0][0] == 0 and spans[-1][1] == count
+            assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
+            assert all(lo % 64 == 0 or lo == count for lo, _ in spans)   # ranks past the end are empty
 
 
 def test_interleave_restores_chunk_order():
@@ -132,6 +158,17 @@ def oracle_partials(og, p, first, count, rank, world):
     return out
 
 
+def oracle_runs(og, p, first, count, rank, world):
+    """This rank's run sums, its block's chunk partials drawn by the oracle."""
+    lo, hi = sharded.rank_samples(count, rank, world)
+    parts = np.zeros((hi - lo + 63) // 64, dtype=api.PARTIAL_DTYPE)
+    for i in range(len(parts)):
+        s0 = first + lo + 64 * i
+        acc, _ = O.ns_run(og, p, seed=SEED, first=s0, count=min(64, first + hi - s0), slot=SLOT)
+        parts[i] = (acc.sum, acc.sumsq, acc.hits, acc.n)
+    return sharded.runs_from_partials(parts, count, rank, world)
+
+
 def _rank_main(rank, world, port, rp, col, out_dir):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -139,7 +176,7 @@ def _rank_main(rank, world, port, rp, col, out_dir):
     try:
         og = O.Graph(rp, col)
         p = O.plan(*G.pattern("4-clique"))
-        res = sharded.estimate_sharded(lambda f, c, r, w: oracle_partials(og, p, f, c, r, w), EPS, DELTA, W,
+        res = sharded.estimate_sharded(lambda f, c, r, w: oracle_runs(og, p, f, c, r, w), EPS, DELTA, W,
                                        rank, world, sharded.torch_gather())
         np.save(os.path.join(out_dir, "r%d.npy" % rank),
                 np.array([res["estimate"], res["eps_hat"], res["samples"], res["hits"], res["rounds"],
@@ -166,7 +203,7 @@ def test_two_gloo_ranks_reproduce_the_online_run(tmp_path):
     assert r0[0] == pytest.approx(o.estimate, rel=1e-12)
     assert r0[1] == pytest.approx(o.eps_hat, rel=1e-10)
     # one process, same chunk partials, merged the same way: identical bits
-    one = sharded.estimate_sharded(lambda f, c, r, w: oracle_partials(og, O.plan(*G.pattern("4-clique")), f, c, r, w),
+    one = sharded.estimate_sharded(lambda f, c, r, w: oracle_runs(og, O.plan(*G.pattern("4-clique")), f, c, r, w),
                                    EPS, DELTA, W, 0, 1, lambda local: [local])
     assert (one["estimate"], one["sum"], one["sumsq"]) == (r0[0], r0[6], r0[7])
 
@@ -178,7 +215,7 @@ def test_checkpoint_and_resume_equal_the_uninterrupted_run():
     rp, col = G.to_numpy(*G.erdos_renyi(300, 0.08, seed=8))
     og = O.Graph(rp, col)
     p = O.plan(*G.pattern("4-clique"))
-    fn = lambda f, c, r, w: oracle_partials(og, p, f, c, r, w)
+    fn = lambda f, c, r, w: oracle_runs(og, p, f, c, r, w)
     gather = lambda local: [local]
     full = sharded.estimate_sharded(fn, EPS, DELTA, W, 0, 1, gather)
     assert full["converged"] == 1 and full["rounds"] >= 3
