@@ -73,6 +73,11 @@ typedef enum {
 /* gpm_load_csr flags */
 #define GPM_DEVICE_PTRS 1u   /* row_ptr/col are device pointers, borrowed for the handle's lifetime */
 #define GPM_VALIDATE    2u   /* check the CSR invariants on the device (GPM_ERR_GRAPH if violated) */
+#define GPM_RELABEL_DEGREE 4u /* relabel vertices by (degree, id) ascending on the device before building the
+                                 index (the orientation the paper applies to cliques, Table tab:input caption;
+                                 the order is this library's reading), into arrays the handle owns; every
+                                 vertex id the library reports afterwards (traces) is a new id, see
+                                 gpm_relabel_map */
 
 /* A connected pattern with k vertices; bit j of adj[i] marks the edge i-j
  * (the matrix must be symmetric without diagonal).  induced = 1 counts
@@ -117,6 +122,11 @@ typedef struct {
                                the start of the run's stream and report their mean algorithmic
                                bytes in gpm_result.algo_bytes_per_sample (0 = skip; not counted
                                in t_total_s) */
+    uint32_t mlp_tensor;    /* learned proposal: 1 = score on the tensor cores (the 64 x 64 layer as
+                               BF16 mma.sync tiles of 16 candidates, FP32 accumulation; layer-1
+                               outputs rounded to BF16), 0 = the exact FP32 chain (default).  The
+                               estimator stays unbiased either way (every score is >= 1) */
+    uint32_t pad_;
 } gpm_config;
 
 /* What the hybrid choice saw (Sec. 4.3-4.4, 5.1): the pilot's sample count
@@ -210,9 +220,18 @@ typedef struct {
 gpm_status gpm_load_csr(uint64_t n, const uint64_t *row_ptr, const uint32_t *col, uint32_t flags,
                         void *stream, gpm_graph **out);
 
+/* Release a handle and every device array it owns (borrowed arrays stay the
+ * caller's).  Library convenience: the paper has no counterpart.  NULL is a
+ * no-op; the handle's stream is synchronised first. */
 void gpm_free_graph(gpm_graph *g);
 
-/* n, m (undirected edges), 2m, maximum degree. Any output may be NULL. */
+/* For a graph loaded with GPM_RELABEL_DEGREE: new_of_old (HOST, n entries)
+ * receives the new id of every vertex as given to gpm_load_csr.  Library
+ * convenience: the paper has no counterpart.  GPM_ERR_ARG without the flag. */
+gpm_status gpm_relabel_map(const gpm_graph *g, uint32_t *new_of_old);
+
+/* n, m (undirected edges), 2m, maximum degree. Any output may be NULL.
+ * Library convenience: the paper has no counterpart. */
 gpm_status gpm_graph_info(const gpm_graph *g, uint64_t *n, uint64_t *m, uint64_t *nnz, uint64_t *max_degree);
 
 /* Estimate the pattern's count to relative error eps with confidence 1-delta.
@@ -382,6 +401,12 @@ gpm_status gpm_exact_count(gpm_graph *g, const gpm_pattern *pattern, uint64_t *o
 /* Scores a_x of n feature rows (DEVICE float [n][3]) into DEVICE out [n];
  * bit-identical to the scores the sampler computes. */
 gpm_status gpm_mlp_scores(gpm_graph *g, const gpm_mlp *mlp, const float *feat, uint64_t n, uint32_t *out);
+
+/* The same rows scored as the sampler does with cfg->mlp_tensor = 1: the 64 x 64
+ * layer as BF16 mma.sync tiles (FP32 accumulation) after rounding the layer-1
+ * outputs to BF16.  Close to, not equal to, gpm_mlp_scores: the difference in
+ * the logit is bounded by the BF16 rounding of the hidden layer. */
+gpm_status gpm_mlp_scores_tc(gpm_graph *g, const gpm_mlp *mlp, const float *feat, uint64_t n, uint32_t *out);
 
 /* Mean binary cross-entropy on the logits over rows (DEVICE feat [rows][3],
  * label [rows] in {0, 1}) at FP32 weights w32 (DEVICE, 4481) and its

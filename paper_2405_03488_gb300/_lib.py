@@ -24,7 +24,7 @@ GPM_ERR_COMM = -9
 
 NS, GS, HYBRID, NS_LEARNED, EXACT = 0, 1, 2, 3, 4
 VERIFY_INTERSECT, VERIFY_CHECK, VERIFY_LAZY = 0, 1, 2
-DEVICE_PTRS, VALIDATE = 1, 2
+DEVICE_PTRS, VALIDATE, RELABEL_DEGREE = 1, 2, 4
 
 STATUS_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_GRAPH", -3: "ERR_OOM", -4: "ERR_CUDA",
                 -5: "ERR_NOT_CONVERGED", -6: "ERR_ABORTED", -8: "ERR_UNSUPPORTED", -9: "ERR_COMM"}
@@ -43,7 +43,8 @@ class Config(C.Structure):
                 ("max_seconds", C.c_double), ("colors", C.c_uint32), ("slot", C.c_uint32),
                 ("verify", C.c_uint32), ("grid_blocks", C.c_uint32), ("block_warps", C.c_uint32),
                 ("cap", C.c_uint32), ("mlp", C.POINTER(MLP)), ("selector", C.POINTER(MLP)),
-                ("edge_p", C.c_double), ("samplers", C.c_uint32), ("bytes_sample", C.c_uint32)]
+                ("edge_p", C.c_double), ("samplers", C.c_uint32), ("bytes_sample", C.c_uint32),
+                ("mlp_tensor", C.c_uint32), ("pad_", C.c_uint32)]
 
 
 class HybridInfo(C.Structure):
@@ -100,6 +101,7 @@ SIGNATURES = [
     ("gpm_load_csr", _i32, [_u64, _V, _V, _u32, _V, P(_V)]),
     ("gpm_free_graph", None, [_V]),
     ("gpm_graph_info", _i32, [_V, P(_u64), P(_u64), P(_u64), P(_u64)]),
+    ("gpm_relabel_map", _i32, [_V, _V]),
     ("gpm_estimate", _i32, [_V, P(Pattern), _i32, _dbl, _dbl, _u64, P(Config), P(Result)]),
     ("gpm_estimate_batch", _i32, [_V, _u32, P(Pattern), P(_dbl), _dbl, _u64, P(Config), P(Result)]),
     ("gpm_autotune", _i32, [_V, _u32, P(Pattern), _u64, P(Config)]),
@@ -117,6 +119,7 @@ SIGNATURES = [
     ("gpm_trace", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), _V]),
     ("gpm_exact_count", _i32, [_V, P(Pattern), P(_u64)]),
     ("gpm_mlp_scores", _i32, [_V, P(MLP), _V, _u64, _V]),
+    ("gpm_mlp_scores_tc", _i32, [_V, P(MLP), _V, _u64, _V]),
     ("gpm_mlp_loss_grad", _i32, [_V, _V, _V, _V, _u64, _V, P(_dbl)]),
     ("gpm_proposal_features", _i32, [_V, P(Pattern), _V, _u64, _V, _V, P(_u64)]),
     ("gpm_train_proposal", _i32, [_V, P(Pattern), _u64, _u64, _u32, _u32, C.c_float, _V, _V, P(_dbl), P(_u64)]),

@@ -8,7 +8,7 @@ import torch
 
 from . import _lib
 from . import graphs as _graphs
-from ._lib import (DEVICE_PTRS, EXACT, GS, HYBRID, NS, NS_LEARNED,  # noqa: F401
+from ._lib import (DEVICE_PTRS, EXACT, GS, HYBRID, NS, NS_LEARNED, RELABEL_DEGREE,  # noqa: F401
                    VALIDATE, VERIFY_CHECK, VERIFY_INTERSECT, VERIFY_LAZY, check, make_pattern)
 
 RECORD_DTYPE = np.dtype([("factor", np.uint64, _lib.MAX_K), ("w_u64", np.uint64), ("w_f64", np.float64),
@@ -68,10 +68,10 @@ class Graph:
     either CUDA tensors, which the handle borrows (kept alive here), or host
     arrays, which the library copies to the device."""
 
-    def __init__(self, row_ptr, col, validate=False):
+    def __init__(self, row_ptr, col, validate=False, relabel=False):
         L = _lib.load()
         self._keep = None
-        flags = VALIDATE if validate else 0
+        flags = (VALIDATE if validate else 0) | (RELABEL_DEGREE if relabel else 0)
         h = C.c_void_p()
         if isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda:
             row_ptr = row_ptr.contiguous().to(torch.int64)
@@ -93,6 +93,12 @@ class Graph:
         n_, m_, nnz_, md_ = C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_uint64()
         check(L.gpm_graph_info(h, C.byref(n_), C.byref(m_), C.byref(nnz_), C.byref(md_)), "gpm_graph_info")
         self.n, self.m, self.nnz, self.max_degree = n_.value, m_.value, nnz_.value, md_.value
+
+    def relabel_map(self):
+        """New id of every loaded vertex (a graph loaded with relabel=True)."""
+        out = np.zeros(max(self.n, 1), dtype=np.uint32)
+        check(_lib.load().gpm_relabel_map(self.h, C.c_void_p(out.ctypes.data)), "gpm_relabel_map")
+        return out[:self.n]
 
     def close(self):
         if getattr(self, "h", None):
@@ -339,13 +345,15 @@ class Proposal:
                                         C.c_void_p(self.w16.data_ptr()), C.byref(loss)), "gpm_mlp_train")
         return loss.value
 
-    def scores(self, graph, feat):
-        """Sampler scores a_x of feature rows (CUDA float tensor [n, 3])."""
+    def scores(self, graph, feat, tensor=False):
+        """Sampler scores a_x of feature rows (CUDA float tensor [n, 3]);
+        tensor=True scores them as the sampler does with mlp_tensor=1."""
         feat = feat.contiguous().float()
         out = torch.empty(feat.shape[0], dtype=torch.int32, device=feat.device)
         m = self.c_struct()
-        check(_lib.load().gpm_mlp_scores(graph.h, C.byref(m), C.c_void_p(feat.data_ptr()), feat.shape[0],
-                                         C.c_void_p(out.data_ptr())), "gpm_mlp_scores")
+        fn = _lib.load().gpm_mlp_scores_tc if tensor else _lib.load().gpm_mlp_scores
+        check(fn(graph.h, C.byref(m), C.c_void_p(feat.data_ptr()), feat.shape[0], C.c_void_p(out.data_ptr())),
+              "gpm_mlp_scores_tc" if tensor else "gpm_mlp_scores")
         return out
 
     def loss_grad(self, graph, feat, label, w32=None):

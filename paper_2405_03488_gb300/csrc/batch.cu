@@ -31,7 +31,7 @@ struct BatchJob {
     uint64_t hits, n;
     double eps, mu, half, eps_hat;
     uint64_t n_min, n_max, rounds;
-    uint32_t slot, active, converged, chunk_off, nchunks, pad;
+    uint32_t slot, active, converged, chunk_off, nchunks, single;   // single: plan has single-list steps
 };
 
 struct BatchCtl {
@@ -39,6 +39,8 @@ struct BatchCtl {
     uint32_t total_chunks;   // chunks of the current round over active jobs
     uint32_t active;         // jobs still running
     uint32_t rounds;         // rounds laid out so far
+    uint32_t any_single;     // some active job needs the single-list sampler variant
+    uint32_t pad;
 };
 
 struct BatchArgs {
@@ -46,6 +48,7 @@ struct BatchArgs {
     double z;
     uint32_t njobs, cap, chunk, chunks_per_job;
     gpm_mlp mlp;
+    uint32_t mlp_tc;
 };
 
 // static shared memory of ns_batch_kernel: one StepPlan per warp
@@ -66,6 +69,7 @@ __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOC
     a.seed = ba.seed;
     a.cap = ba.cap;
     a.trace = nullptr;
+    a.mlp_tc = ba.mlp_tc;
     for (;;) {
         unsigned c = 0;
         if (lane == 0) c = atomicAdd(&ctl->counter, 1u);
@@ -165,19 +169,21 @@ __global__ void __launch_bounds__(1024) batch_reduce_check(const Partial *__rest
 
 __global__ void batch_relayout(BatchJob *jobs, BatchCtl *ctl, const BatchArgs ba) {
     if (threadIdx.x != 0) return;
-    uint32_t off = 0, act = 0;
+    uint32_t off = 0, act = 0, single = 0;
     for (uint32_t q = 0; q < ba.njobs; q++) {
         if (jobs[q].active) {
             jobs[q].chunk_off = off;
             jobs[q].nchunks = ba.chunks_per_job;
             off += ba.chunks_per_job;
             act++;
+            single |= jobs[q].single;
         } else {
             jobs[q].nchunks = 0;
         }
     }
     ctl->total_chunks = off;
     ctl->active = act;
+    ctl->any_single = single;
     ctl->counter = 0;
     ctl->rounds += 1;
 }
@@ -243,6 +249,7 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
     ba.chunks_per_job = (uint32_t)cpj;
     std::memset(&ba.mlp, 0, sizeof(ba.mlp));
     if (mode == MODE_LEARNED) ba.mlp = *cfg->mlp;
+    ba.mlp_tc = (mode == MODE_LEARNED && cfg->mlp_tensor) ? 1u : 0u;
 
     std::vector<BatchJob> jobs(nj);
     for (uint32_t q = 0; q < nj; q++) {
@@ -256,16 +263,17 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
         J.chunk_off = (uint32_t)(q * cpj);
         J.nchunks = (uint32_t)cpj;
         J.eps_hat = INFINITY;
+        J.single = plan_single_steps(plans[q]) ? 1u : 0u;
     }
-    BatchCtl ctl{0u, (uint32_t)(cpj * nj), nj, 0u};
+    BatchCtl ctl{0u, (uint32_t)(cpj * nj), nj, 0u, 1u, 0u};
 
     Plan *d_plans = nullptr;
     BatchJob *d_jobs = nullptr;
     BatchCtl *d_ctl = nullptr;
     Partial *d_parts = nullptr;
     cudaStream_t cs = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr, graph_plain = nullptr;
+    cudaGraphExec_t exec = nullptr, exec_plain = nullptr;
     cudaEvent_t ev_in = nullptr, ev_a = nullptr, ev_b = nullptr;
     const int R = 4;   // rounds per graph launch
     cudaEvent_t ev_k[2 * R] = {};
@@ -274,6 +282,8 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
     auto cleanup = [&]() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        if (exec_plain) cudaGraphExecDestroy(exec_plain);
+        if (graph_plain) cudaGraphDestroy(graph_plain);
         // stream-ordered frees after the batch's own work
         cudaStream_t fs = cs ? cs : h->stream;
         pool_free(d_plans, fs);
@@ -308,56 +318,66 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(BatchJob) * nj, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_ctl, &ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
-    uint32_t blocks = 0;
-    if (e == cudaSuccess)
-        e = (kmode == MODE_CHECK)     ? batch_grid<MODE_CHECK, false>(h, sh, &blocks)
-            : (kmode == MODE_LAZY)    ? batch_grid<MODE_LAZY, false>(h, sh, &blocks)
-            : (kmode == MODE_LEARNED) ? batch_grid<MODE_LEARNED, false>(h, sh, &blocks)
-            : (kmode == MODE_INTERSECT_SINGLE)
-                ? (compact ? batch_grid<MODE_INTERSECT_SINGLE, true>(h, sh, &blocks)
-                           : batch_grid<MODE_INTERSECT_SINGLE, false>(h, sh, &blocks))
-                : (compact ? batch_grid<MODE_INTERSECT, true>(h, sh, &blocks)
-                           : batch_grid<MODE_INTERSECT, false>(h, sh, &blocks));
-    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
+    // R rounds (sampler, reduce-and-check, relayout) of one compiled sampler
+    // variant captured into a graph
+    auto capture = [&](int km, cudaGraph_t *gr, cudaGraphExec_t *ex) -> cudaError_t {
+        uint32_t blocks = 0;
+        cudaError_t ce = (km == MODE_CHECK)     ? batch_grid<MODE_CHECK, false>(h, sh, &blocks)
+                         : (km == MODE_LAZY)    ? batch_grid<MODE_LAZY, false>(h, sh, &blocks)
+                         : (km == MODE_LEARNED) ? batch_grid<MODE_LEARNED, false>(h, sh, &blocks)
+                         : (km == MODE_INTERSECT_SINGLE)
+                             ? (compact ? batch_grid<MODE_INTERSECT_SINGLE, true>(h, sh, &blocks)
+                                        : batch_grid<MODE_INTERSECT_SINGLE, false>(h, sh, &blocks))
+                             : (compact ? batch_grid<MODE_INTERSECT, true>(h, sh, &blocks)
+                                        : batch_grid<MODE_INTERSECT, false>(h, sh, &blocks));
+        if (ce == cudaSuccess) ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) return ce;
         const size_t smem = smem_bytes(sh, mode);
+        const dim3 grid(blocks), block(sh.warps * 32);
         for (int r = 0; r < R; r++) {
             // event nodes around each sampler launch time the sampler alone
             cudaEventRecordWithFlags(ev_k[2 * r], cs, cudaEventRecordExternal);
-            if (kmode == MODE_CHECK)
-                ns_batch_kernel<MODE_CHECK, false>
-                    <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
-            else if (kmode == MODE_LAZY)
-                ns_batch_kernel<MODE_LAZY, false>
-                    <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
-            else if (kmode == MODE_LEARNED)
+            if (km == MODE_CHECK)
+                ns_batch_kernel<MODE_CHECK, false><<<grid, block, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
+            else if (km == MODE_LAZY)
+                ns_batch_kernel<MODE_LAZY, false><<<grid, block, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
+            else if (km == MODE_LEARNED)
                 ns_batch_kernel<MODE_LEARNED, false>
-                    <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
-            else if (kmode == MODE_INTERSECT_SINGLE && compact)
+                    <<<grid, block, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
+            else if (km == MODE_INTERSECT_SINGLE && compact)
                 ns_batch_kernel<MODE_INTERSECT_SINGLE, true>
-                    <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
-            else if (kmode == MODE_INTERSECT_SINGLE)
+                    <<<grid, block, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
+            else if (km == MODE_INTERSECT_SINGLE)
                 ns_batch_kernel<MODE_INTERSECT_SINGLE, false>
-                    <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
+                    <<<grid, block, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
             else if (compact)
                 ns_batch_kernel<MODE_INTERSECT, true>
-                    <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
+                    <<<grid, block, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
             else
                 ns_batch_kernel<MODE_INTERSECT, false>
-                    <<<blocks, sh.warps * 32, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
+                    <<<grid, block, smem, cs>>>(h->d, d_plans, d_jobs, d_ctl, ba, d_parts);
             cudaEventRecordWithFlags(ev_k[2 * r + 1], cs, cudaEventRecordExternal);
             batch_reduce_check<<<nj, 1024, 0, cs>>>(d_parts, d_jobs, ba);
             batch_relayout<<<1, 32, 0, cs>>>(d_jobs, d_ctl, ba);
         }
-        cudaError_t ec = cudaStreamEndCapture(cs, &graph);
-        if (e == cudaSuccess) e = ec;
+        ce = cudaStreamEndCapture(cs, gr);
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(ex, *gr, 0);
+        return ce;
+    };
+    if (e == cudaSuccess) e = capture(kmode, &graph, &exec);
+    // a batch that mixes plans with and without single-list steps switches to
+    // the smaller plain variant once no job that needs the other is running
+    if (e == cudaSuccess && kmode == MODE_INTERSECT_SINGLE) {
+        bool all_single = true;
+        for (const Plan &pl : plans) all_single = all_single && plan_single_steps(pl);
+        if (!all_single) e = capture(MODE_INTERSECT, &graph_plain, &exec_plain);
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     std::vector<float> round_ms;
     uint64_t launches = 0;
+    cudaGraphExec_t cur = exec;
     while (e == cudaSuccess) {
         e = cudaEventRecord(ev_a, cs);
-        if (e == cudaSuccess) e = cudaGraphLaunch(exec, cs);
+        if (e == cudaSuccess) e = cudaGraphLaunch(cur, cs);
         if (e == cudaSuccess) e = cudaEventRecord(ev_b, cs);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, cs);
         if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
@@ -369,6 +389,7 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
         }
         launches += 3 * R;
         if (ctl.active == 0) break;
+        if (exec_plain && !ctl.any_single) cur = exec_plain;
         if (h->abort_flag) {
             status = GPM_ERR_ABORTED;
             set_error("aborted");

@@ -357,6 +357,24 @@ extern "C" gpm_status gpm_load_csr(uint64_t n, const uint64_t *row_ptr, const ui
         set_error(std::string("gpm_load_csr: invalid CSR: ") + kValidateMsg[bad_h < 6 ? bad_h : 0]);
         return fail(GPM_ERR_GRAPH);
     }
+    if (e == cudaSuccess && (flags & GPM_RELABEL_DEGREE)) {
+        uint64_t *nrp = nullptr;
+        uint32_t *ncol = nullptr, *nid = nullptr;
+        const gpm_status rs = relabel_by_degree(n, nnz, g->d.row_ptr, g->d.col, st, &nrp, &ncol, &nid);
+        if (rs != GPM_OK) {
+            pool_free(bad, st);
+            pool_free(maxd, st);
+            return fail(rs);
+        }
+        // the handle's own copy is replaced; a borrowed CSR stays the caller's
+        pool_free(g->own_row_ptr, st);
+        pool_free(g->own_col, st);
+        g->own_row_ptr = nrp;
+        g->own_col = ncol;
+        g->d.row_ptr = nrp;
+        g->d.col = ncol;
+        g->newid = nid;
+    }
     uint64_t *cnt = nullptr;
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&cnt, sizeof(uint64_t) * (n + 1), st);
     if (e == cudaSuccess && n > 0) {
@@ -415,6 +433,7 @@ extern "C" void gpm_free_graph(gpm_graph *g) {
     pool_free(g->up, g->stream);
     pool_free(g->uoff, g->stream);
     pool_free(g->edges, g->stream);
+    pool_free(g->newid, g->stream);
     pool_free(g->partials, g->stream);
     pool_free(g->totals, g->stream);
     pool_free(g->counter, g->stream);
@@ -422,6 +441,25 @@ extern "C" void gpm_free_graph(gpm_graph *g) {
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     delete g;
+}
+
+extern "C" gpm_status gpm_relabel_map(const gpm_graph *g, uint32_t *new_of_old) {
+    if (!g || !new_of_old) {
+        set_error("gpm_relabel_map: null argument");
+        return GPM_ERR_ARG;
+    }
+    if (!g->newid) {
+        set_error("gpm_relabel_map: the graph was loaded without GPM_RELABEL_DEGREE");
+        return GPM_ERR_ARG;
+    }
+    if (g->d.n == 0) return GPM_OK;
+    cudaError_t e = cudaMemcpyAsync(new_of_old, g->newid, sizeof(uint32_t) * g->d.n, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("gpm_relabel_map: ") + cudaGetErrorString(e));
+        return GPM_ERR_CUDA;
+    }
+    return GPM_OK;
 }
 
 extern "C" gpm_status gpm_graph_info(const gpm_graph *g, uint64_t *n, uint64_t *m, uint64_t *nnz,

@@ -134,6 +134,8 @@ gpm_status sparsify_alloc(gpm_graph *h, uint32_t c, uint64_t seed, uint32_t colo
 double normal_quantile(double p);
 gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const double *eps, double delta,
                           uint64_t seed, const gpm_config *cfg, gpm_result *results, int mode);
+gpm_status relabel_by_degree(uint64_t n, uint64_t nnz, const uint64_t *row_ptr, const uint32_t *col,
+                             cudaStream_t st, uint64_t **row_out, uint32_t **col_out, uint32_t **newid_out);
 gpm_status algo_bytes_mean(gpm_graph *h, const Plan &p, int mode, uint64_t seed, uint32_t slot,
                            const gpm_config *cfg, uint64_t count, double *out);
 }  // namespace gpm
@@ -148,6 +150,7 @@ struct gpm_graph {
     uint32_t *own_col;
     uint64_t *up, *uoff;
     uint64_t *edges;              // materialised oriented edges (optional)
+    uint32_t *newid;              // GPM_RELABEL_DEGREE: new id of every loaded vertex (else null)
     // sampler scratch
     gpm::Partial *partials;
     uint64_t partials_cap;

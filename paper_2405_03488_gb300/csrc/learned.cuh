@@ -17,6 +17,16 @@ __device__ __forceinline__ float flog2p1(uint64_t d) {
     return __fadd_rn(__int2float_rn(e), frac);
 }
 
+// The score mapping of a logit z: s = clamp(z / 8 + 1/2, 0, 1), a = 1 + floor(4096 s).
+__device__ __forceinline__ uint32_t score_of_logit(float z) {
+    float sc = __fmaf_rn(z, 0.125f, 0.5f);
+    if (!(sc > 0.f)) sc = 0.f;
+    if (sc > 1.f) sc = 1.f;
+    return 1u + (uint32_t)floorf(__fmul_rn(sc, 4096.0f));
+}
+
+__device__ __forceinline__ uint32_t bf16_bits(float x) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+
 // Score of one candidate, computed by one lane alone: the 3 -> 64 -> 64 -> 1
 // ReLU MLP with FP32 fused multiply-adds in input order (hidden layer 2 and
 // the output chain walk the units in ascending order, as the oracle does),
@@ -56,10 +66,90 @@ __device__ __forceinline__ uint32_t mlp_score_lane(const float *W, float f0, flo
         z = __fmaf_rn(w3[o], acc_a > 0.f ? acc_a : 0.f, z);
         z = __fmaf_rn(w3[o + 1], acc_b > 0.f ? acc_b : 0.f, z);
     }
-    float sc = __fmaf_rn(z, 0.125f, 0.5f);
-    if (!(sc > 0.f)) sc = 0.f;
-    if (sc > 1.f) sc = 1.f;
-    return 1u + (uint32_t)floorf(__fmul_rn(sc, 4096.0f));
+    return score_of_logit(z);
+}
+
+// D += A B for one m16n8k16 tile: A 16x16 BF16 (row-major), B 16x8 BF16
+// (column-major), D 16x8 FP32; fragments in the PTX ISA's register layout.
+__device__ __forceinline__ void mma_bf16_16816(float d[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Scores of 16 candidates (rows) with the 64 x 64 layer on the tensor cores
+// (the warp calls it together).  feat(c, &f0, &f1, &f2) gives candidate c's
+// features.  Layer 1 runs in FP32 (lane l: candidate l mod 16, hidden units
+// 32 (l / 16) .. + 31) and is rounded to BF16 into the warp's tile; layer 2
+// is 8 x 4 mma.sync m16n8k16 (BF16 products, FP32 accumulation); bias, ReLU
+// and the output layer follow in FP32, reduced over the 4 lanes that share a
+// row.  Writes score[c] for c < n.  Not bit-identical to the FP32 chain of
+// mlp_score_lane: its h1 is rounded to BF16 and the sums run in the tensor
+// cores' order.
+template <typename Feat>
+__device__ __forceinline__ void mlp_scores_tc(const WarpMem &wm, uint32_t n, Feat feat, uint32_t *score) {
+    const unsigned lane = lane_id();
+    const float *w1 = wm.W, *b1 = wm.W + 192, *b2 = wm.W + 4352, *w3 = wm.W + 4416, *b3 = wm.W + 4480;
+    uint16_t *H = wm.htile;
+    {
+        const uint32_t c = lane & 15u, o0 = (lane >> 4) * 32;
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+        if (c < n) feat(c, &f0, &f1, &f2);
+        uint32_t *row = reinterpret_cast<uint32_t *>(H + c * kW2Stride + o0);
+#pragma unroll
+        for (int o = 0; o < 32; o += 2) {
+            float h[2];
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                const int u = o0 + o + q;
+                float acc = b1[u];
+                acc = __fmaf_rn(w1[u * 3 + 0], f0, acc);
+                acc = __fmaf_rn(w1[u * 3 + 1], f1, acc);
+                acc = __fmaf_rn(w1[u * 3 + 2], f2, acc);
+                h[q] = acc > 0.f ? acc : 0.f;
+            }
+            row[o / 2] = bf16_bits(h[0]) | (bf16_bits(h[1]) << 16);
+        }
+    }
+    __syncwarp();
+    const unsigned gq = lane >> 2, tq = lane & 3u;
+    float d[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 4; ks++) {
+        const uint32_t *r0 = reinterpret_cast<const uint32_t *>(H + gq * kW2Stride + ks * 16 + tq * 2);
+        const uint32_t *r1 = reinterpret_cast<const uint32_t *>(H + (gq + 8) * kW2Stride + ks * 16 + tq * 2);
+        const uint32_t a0 = r0[0], a1 = r1[0], a2 = r0[4], a3 = r1[4];
+#pragma unroll
+        for (int nt = 0; nt < 8; nt++) {
+            const uint32_t *bw = reinterpret_cast<const uint32_t *>(wm.W2b + (nt * 8 + gq) * kW2Stride + ks * 16 +
+                                                                    tq * 2);
+            mma_bf16_16816(d[nt], a0, a1, a2, a3, bw[0], bw[4]);
+        }
+    }
+    float z0 = 0.f, z1 = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++)
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int o = nt * 8 + tq * 2 + q;
+            const float h0 = __fadd_rn(d[nt][q], b2[o]), h1 = __fadd_rn(d[nt][2 + q], b2[o]);
+            z0 = __fmaf_rn(w3[o], h0 > 0.f ? h0 : 0.f, z0);
+            z1 = __fmaf_rn(w3[o], h1 > 0.f ? h1 : 0.f, z1);
+        }
+    z0 = __fadd_rn(z0, __shfl_xor_sync(kFull, z0, 1));
+    z0 = __fadd_rn(z0, __shfl_xor_sync(kFull, z0, 2));
+    z1 = __fadd_rn(z1, __shfl_xor_sync(kFull, z1, 1));
+    z1 = __fadd_rn(z1, __shfl_xor_sync(kFull, z1, 2));
+    if (tq == 0) {
+        if (gq < n) score[gq] = score_of_logit(__fadd_rn(z0, b3[0]));
+        if (gq + 8 < n) score[gq + 8] = score_of_logit(__fadd_rn(z1, b3[0]));
+    }
+    __syncwarp();
 }
 
 // |S_{j+1}| if candidate Sj[ix] were chosen as v_j.  When S_{j+1} extends S_j
@@ -146,7 +236,7 @@ static __device__ __noinline__ uint64_t lookahead_count(const DGraph &g, const P
 template <typename PlanT>
 static __device__ __noinline__ uint32_t learned_pick(const DGraph &g, const PlanT &p, const WarpMem &wm, const uint32_t *Sj,
                                               uint32_t sz, int j, uint64_t r, uint64_t lb, uint64_t le,
-                                              uint64_t *A_out, uint32_t *a_out) {
+                                              bool tc, uint64_t *A_out, uint32_t *a_out) {
     const unsigned lane = lane_id();
     // every candidate's CSR offsets in one pass over the lanes
     uint64_t *cb = reinterpret_cast<uint64_t *>(wm.score + kLearnedMax);
@@ -167,19 +257,37 @@ static __device__ __noinline__ uint32_t learned_pick(const DGraph &g, const Plan
         if (lane == 0) cu[i] = (uint32_t)nxt;
     }
     __syncwarp();
-    // scores, one candidate per lane
     uint64_t A = 0;
     const float fj = __int2float_rn(j);
-    for (uint32_t base = 0; base < sz; base += 32) {
-        const uint32_t i = base + lane;
-        uint32_t a = 0;
-        if (i < sz) {
-            a = mlp_score_lane(wm.W, flog2p1(cd[i]), fj, flog2p1(cu[i]));
-            wm.score[i] = a;
+    if (tc) {
+        // scores, 16 candidates per tensor-core tile
+        for (uint32_t base = 0; base < sz; base += 16) {
+            auto feat = [&](uint32_t c, float *f0, float *f1, float *f2) {
+                *f0 = flog2p1(cd[base + c]);
+                *f1 = fj;
+                *f2 = flog2p1(cu[base + c]);
+            };
+            mlp_scores_tc(wm, sz - base < 16 ? sz - base : 16, feat, wm.score + base);
         }
+        for (uint32_t base = 0; base < sz; base += 32) {
+            uint32_t a = base + lane < sz ? wm.score[base + lane] : 0u;
 #pragma unroll
-        for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
-        A += a;
+            for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+            A += a;
+        }
+    } else {
+        // scores, one candidate per lane
+        for (uint32_t base = 0; base < sz; base += 32) {
+            const uint32_t i = base + lane;
+            uint32_t a = 0;
+            if (i < sz) {
+                a = mlp_score_lane(wm.W, flog2p1(cd[i]), fj, flog2p1(cu[i]));
+                wm.score[i] = a;
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+            A += a;
+        }
     }
     __syncwarp();
     const uint64_t t = index_map(r, A);

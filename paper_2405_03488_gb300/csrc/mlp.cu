@@ -46,6 +46,28 @@ __global__ void __launch_bounds__(256) mlp_score_kernel(const gpm_mlp mlp, const
     for (uint64_t r = t0; r < n; r += nt) out[r] = mlp_score_lane(wm.W, feat[3 * r], feat[3 * r + 1], feat[3 * r + 2]);
 }
 
+// Scores on the tensor cores, 16 rows per warp and tile (the sampler's
+// tensor-core scoring, mlp_scores_tc).
+__global__ void __launch_bounds__(256) mlp_score_tc_kernel(const gpm_mlp mlp, const float *__restrict__ feat,
+                                                           uint64_t n, uint32_t *out) {
+    extern __shared__ __align__(16) uint64_t smem64[];
+    WarpMem wm = warp_mem<MODE_LEARNED>(smem64, 0, mlp);
+    const unsigned lane = lane_id();
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t base = warp * 16; base < n; base += nw * 16) {
+        const uint32_t cnt = (n - base < 16) ? (uint32_t)(n - base) : 16u;
+        auto f = [&](uint32_t c, float *f0, float *f1, float *f2) {
+            *f0 = feat[3 * (base + c)];
+            *f1 = feat[3 * (base + c) + 1];
+            *f2 = feat[3 * (base + c) + 2];
+        };
+        mlp_scores_tc(wm, cnt, f, wm.score);
+        if (lane < cnt) out[base + lane] = wm.score[lane];
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------------ features
 // rows per record: steps 2 <= j <= k-2 that the sample passed
 __global__ void feature_count(const gpm_sample_record *__restrict__ recs, uint64_t n, int k, uint64_t *cnt) {
@@ -374,6 +396,23 @@ extern "C" gpm_status gpm_mlp_scores(gpm_graph *h, const gpm_mlp *mlp, const flo
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     return e == cudaSuccess ? GPM_OK : cuda_fail("gpm_mlp_scores", e);
+}
+
+extern "C" gpm_status gpm_mlp_scores_tc(gpm_graph *h, const gpm_mlp *mlp, const float *feat, uint64_t n,
+                                        uint32_t *out) {
+    if (!h || !mlp || (n && (!feat || !out))) {
+        set_error("gpm_mlp_scores_tc: null argument");
+        return GPM_ERR_ARG;
+    }
+    if (n == 0) return GPM_OK;
+    const size_t smem = kMlpSmemFloats * sizeof(float) + 8 * (kWarpHeaderWords + kLearnedWarpWords) * 4;
+    cudaFuncSetAttribute(mlp_score_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    uint64_t blocks = (n + 127) / 128;
+    if (blocks > (uint64_t)h->sm_count * 16) blocks = (uint64_t)h->sm_count * 16;
+    mlp_score_tc_kernel<<<(unsigned)blocks, 256, smem, h->stream>>>(*mlp, feat, n, out);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? GPM_OK : cuda_fail("gpm_mlp_scores_tc", e);
 }
 
 extern "C" gpm_status gpm_mlp_loss_grad(gpm_graph *h, const float *w32, const float *feat, const float *label,

@@ -309,6 +309,7 @@ static gpm_status run_block(gpm_graph *h, const Plan &p, int mode, uint64_t seed
     a.stride = world;
     std::memset(&a.mlp, 0, sizeof(a.mlp));
     if (mode == MODE_LEARNED) a.mlp = *cfg->mlp;
+    a.mlp_tc = (mode == MODE_LEARNED && cfg->mlp_tensor) ? 1u : 0u;
     if (cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), h->stream) != cudaSuccess) {
         set_error("cudaMemsetAsync failed");
         return GPM_ERR_CUDA;
@@ -1125,6 +1126,7 @@ extern "C" gpm_status gpm_sample_sums_static(gpm_graph *h, const gpm_pattern *pa
     a.stride = 1;
     std::memset(&a.mlp, 0, sizeof(a.mlp));
     if (mode == MODE_LEARNED) a.mlp = *cfg->mlp;
+    a.mlp_tc = (mode == MODE_LEARNED && cfg->mlp_tensor) ? 1u : 0u;
     cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess)
         e = launch_mode<false>(h, p, sh, a, kernel_mode(mode, plan_single_steps(p)));

@@ -4,6 +4,7 @@
 
 #include <type_traits>
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,10 +39,14 @@ constexpr uint32_t kLearnedMax = 256;   // larger candidate sets are drawn unifo
 #endif
 
 constexpr int kMlpFloats = 4481;        // 3->64->64->1 weights and biases
-constexpr int kMlpSmemFloats = 4482;    // padded to 8 bytes
-// hidden activations, scores, and each candidate's CSR offsets (u64 row start,
-// u32 degree, u32 offset of its first neighbour above itself)
-constexpr int kLearnedWarpWords = 128 + kLearnedMax + 4 * kLearnedMax;
+constexpr int kW2Stride = 72;           // BF16 W2 rows and hidden tiles, padded against bank conflicts
+// the FP32 weights (padded to 8 bytes), then W2 as raw BF16, 64 rows of kW2Stride
+constexpr int kMlpSmemFloats = 4482 + 64 * kW2Stride / 2;
+// the BF16 hidden tile of 16 candidates (tensor-core scoring), scores, and
+// each candidate's CSR offsets (u64 row start, u32 degree, u32 offset of its
+// first neighbour above itself)
+constexpr int kHTileWords = 16 * kW2Stride / 2;
+constexpr int kLearnedWarpWords = kHTileWords + kLearnedMax + 4 * kLearnedMax;
 
 struct RunArgs {
     uint64_t seed;
@@ -56,6 +61,7 @@ struct RunArgs {
     uint32_t nchunks;
     uint32_t stride;              // chunks of the range between consecutive chunks of this launch
     gpm_mlp mlp;                  // learned proposal weights (device, BF16)
+    uint32_t mlp_tc;              // learned: score on the tensor cores (mma.sync BF16)
 };
 
 // The fields of a Plan the sampler reads, for an on-chip copy per warp.
@@ -82,16 +88,23 @@ __device__ __forceinline__ void load_step_plan(const Plan &src, StepPlan *dst) {
     __syncwarp();
 }
 
-constexpr int kWarpHeaderWords = 52;   // 12 u64 factors + 16 u32 vertices + 12 u32 scores
+// 12 u64 factors + 16 u32 vertices + 12 u32 scores, then the step-2 test table:
+// 9 u64 list starts, 9 u32 lengths (top bit: the list must not hold y), 9 u32
+// vertices y must differ from
+constexpr int kWarpHeaderWords = 88;
+constexpr int kTestSlots = 9;   // positions before the last of a 10-vertex pattern
 
 struct WarpMem {
     uint64_t *fac;
     uint32_t *v;
     uint32_t *aux;
+    uint64_t *tptr;        // step-2 test table (see kWarpHeaderWords)
+    uint32_t *tlen, *tneq;
     uint32_t *S0, *S1;
-    float *hbuf;           // learned: 64 + 64 hidden activations
+    uint16_t *htile;       // learned, tensor cores: BF16 layer-1 outputs of 16 candidates
     uint32_t *score;       // learned: a_x of each candidate
-    const float *W;        // learned: block copy of the weights (W2 transposed)
+    const float *W;        // learned: block copy of the weights (FP32, gpm_mlp order)
+    const uint16_t *W2b;   // learned: W2 as raw BF16, rows of kW2Stride
 };
 
 // Block-level setup: the learned weights (BF16 -> FP32, in the gpm_mlp order;
@@ -110,6 +123,11 @@ __device__ __forceinline__ WarpMem warp_mem(uint64_t *smem64, uint32_t cap, cons
             else if (i < 4480) W[i] = bf(mlp.w3, i - 4416);
             else W[i] = bf(mlp.b3, 0);
         }
+        uint16_t *W2b = reinterpret_cast<uint16_t *>(W + 4482);
+        for (int i = threadIdx.x; i < 64 * kW2Stride; i += blockDim.x) {
+            const int o = i / kW2Stride, in = i % kW2Stride;
+            W2b[i] = in < 64 ? mlp.w2[o * 64 + in] : (uint16_t)0;
+        }
         __syncthreads();
         smem += kMlpSmemFloats;
     }
@@ -120,11 +138,15 @@ __device__ __forceinline__ WarpMem warp_mem(uint64_t *smem64, uint32_t cap, cons
     wm.fac = reinterpret_cast<uint64_t *>(base);
     wm.v = base + 24;
     wm.aux = base + 40;
+    wm.tptr = reinterpret_cast<uint64_t *>(base + 52);
+    wm.tlen = base + 70;
+    wm.tneq = base + 79;
     wm.S0 = base + kWarpHeaderWords;
     wm.S1 = wm.S0 + cap;
-    wm.hbuf = reinterpret_cast<float *>(wm.S1 + cap);
-    wm.score = wm.S1 + cap + 128;
+    wm.htile = reinterpret_cast<uint16_t *>(wm.S1 + cap);
+    wm.score = wm.S1 + cap + kHTileWords;
     wm.W = W;
+    wm.W2b = reinterpret_cast<const uint16_t *>(W + 4482);
     return wm;
 }
 
@@ -474,49 +496,38 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                         __syncwarp();
                     }
                 }
-                // every condition of S_j but membership in the driver list
+                int ntest = 0, nneq = 0;
+                // every condition of S_j but membership in the driver list,
+                // gathered once per step into the warp's test table: lane i
+                // enters its own list when y must (edge, not the driver or the
+                // staged partner) or must not (vertex-induced non-edge) lie in
+                // it, and its vertex when y could equal it (a non-edge not
+                // below the bound y already exceeds; membership in N(v_i)
+                // rules out y = v_i, the graph having no loops)
+                {
+                    const bool edge = (int)lane < j && ((back >> lane) & 1u);
+                    const bool nonedge = (int)lane < j && !edge;
+                    const bool test = (edge && (int)lane != driver && (int)lane != staged) || (nonedge && p.induced);
+                    const bool neq = nonedge && !(has_lo && wm.v[lane] <= lo);
+                    const unsigned tm = __ballot_sync(kFull, test), nm = __ballot_sync(kFull, neq);
+                    if (test) {
+                        const int t = __popc(tm & lanemask_lt());
+                        wm.tptr[t] = lb;
+                        wm.tlen[t] = (uint32_t)(le - lb) | (nonedge ? 0x80000000u : 0u);
+                    }
+                    if (neq) wm.tneq[__popc(nm & lanemask_lt())] = wm.v[lane];
+                    ntest = __popc(tm);
+                    nneq = __popc(nm);
+                    __syncwarp();
+                }
                 auto pred = [&](uint32_t y) -> bool {
                     bool ok = true;
-                    for (int i = 0; i < j; i++) {
-                        const uint64_t b = __shfl_sync(kFull, lb, i);
-                        const uint64_t en2 = __shfl_sync(kFull, le, i);
-                        ok = ok && (y != wm.v[i]);
-                        const bool edge = (back >> i) & 1u;
-                        if (edge) {
-                            if (i == driver) continue;
-                            if (i == staged) ok = ok && lane_contains_shared(Sp, plen, y);
-                            else ok = ok && lane_contains(g.col + b, en2 - b, y);
-                        } else if (p.induced) {
-                            ok = ok && !lane_contains(g.col + b, en2 - b, y);
-                        }
-                    }
-                    return ok;
-                };
-                // the same conditions gathered once per step for edge-induced
-                // plans: y must lie in the non-driver back-neighbour lists (the
-                // staged one and at most one in global memory) and differ from
-                // the earlier vertices not below the bound it already exceeds
-                // (membership in N(v_i) rules out y = v_i, the graph having no
-                // loops); pred covers every other case
-                uint32_t gmask = 0, nmask = 0;
-                if (kCompact) {
-                    for (int i = 0; i < j; i++) {
-                        const bool edge = (back >> i) & 1u;
-                        if (edge && i != driver && i != staged) gmask |= 1u << i;
-                        if (!edge && !(has_lo && wm.v[i] <= lo)) nmask |= 1u << i;
-                    }
-                }
-                const bool fast = kCompact && !p.induced && __popc(gmask) <= 1 && __popc(nmask) <= 1;
-                const int gi = gmask ? __ffs(gmask) - 1 : 0;
-                const uint64_t fb = __shfl_sync(kFull, lb, gi);
-                const uint32_t *const fptr = g.col + fb;
-                const uint32_t flen = gmask ? (uint32_t)(__shfl_sync(kFull, le, gi) - fb) : 0u;
-                if (gmask && flen == 0) empty = true;   // S_j lies inside that list
-                const uint32_t nv = nmask ? wm.v[__ffs(nmask) - 1] : 0xFFFFFFFFu;   // no vertex has this id
-                auto fast_pred = [&](uint32_t y) -> bool {
-                    bool ok = y != nv;
+                    for (int t = 0; t < nneq; t++) ok = ok && y != wm.tneq[t];
                     if (staged >= 0) ok = ok && lane_contains_shared(Sp, plen, y);
-                    if (flen) ok = ok && lane_contains(fptr, flen, y);
+                    for (int t = 0; t < ntest; t++) {
+                        const uint32_t ln = wm.tlen[t];
+                        ok = ok && (lane_contains(g.col + wm.tptr[t], ln & 0x7FFFFFFFu, y) != (ln >> 31));
+                    }
                     return ok;
                 };
                 if (!empty) {
@@ -533,7 +544,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                         for (int u = 0; u < 4; u++) {
                             if (base + 32 * u >= de) break;
                             const uint32_t yu = u == 0 ? y[0] : u == 1 ? y[1] : u == 2 ? y[2] : y[3];
-                            const bool ok = (fast ? fast_pred(yu) : pred(yu)) && (base + 32 * u + lane < de);
+                            const bool ok = pred(yu) && (base + 32 * u + lane < de);
                             const unsigned m = __ballot_sync(kFull, ok);
                             if (ok) {
                                 const uint64_t pos = count + __popc(m & lanemask_lt());
@@ -573,7 +584,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                                 for (int u = 0; u < 4; u++) {
                                     if (found || base + 32 * u >= de) break;
                                     const uint32_t yu = u == 0 ? y[0] : u == 1 ? y[1] : u == 2 ? y[2] : y[3];
-                                    const bool ok = (fast ? fast_pred(yu) : pred(yu)) && (base + 32 * u + lane < de);
+                                    const bool ok = pred(yu) && (base + 32 * u + lane < de);
                                     const unsigned m = __ballot_sync(kFull, ok);
                                     const uint64_t c = __popc(m);
                                     if (seen + c > target) {
@@ -629,7 +640,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
             if (MODE == MODE_LEARNED && j <= k - 2 && mat && size <= kLearnedMax) {
                 uint64_t A = 0;
                 uint32_t ax = 0;
-                x = learned_pick(g, p, wm, Sc, (uint32_t)size, j, r, lb, le, &A, &ax);
+                x = learned_pick(g, p, wm, Sc, (uint32_t)size, j, r, lb, le, a.mlp_tc != 0, &A, &ax);
                 if (lane == 0) {
                     wm.fac[j] = A;
                     wm.aux[j] = ax;

@@ -169,3 +169,71 @@ def test_trained_proposal_gains_over_plain_and_stays_unbiased():
     # the gain: more hits and a smaller per-sample variance
     assert hl > hp
     assert vl < vp
+
+
+# ------------------------------------------------------------------ tensor-core scoring (mlp_tensor = 1)
+def _bf16_round(x):
+    """Round float32 values to BF16 (nearest even), returned as float64."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
+    return (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def test_tensor_core_scores_within_the_bf16_bound():
+    """The tensor-core scores differ from the FP32 oracle's only through the BF16
+    rounding of the layer-1 outputs (relative error <= 2^-9 each) and the
+    summation order: per row, |dz| <= sum_o |w3_o| (2^-8 sum_i |W2_oi h1_i|) +
+    2^-18 sum_o |w3_o h2_o|, and a = 1 + floor(512 z + 2048) moves by at most
+    512 |dz| + 1."""
+    rp, col = G.complete(5)
+    g = api.Graph(rp.cuda(), col.cuda())
+    rng = np.random.default_rng(4)
+    feat = np.concatenate([rng.uniform(0, 22, (2000, 3)),
+                           np.stack([rng.integers(0, 20, 500), rng.integers(2, 9, 500),
+                                     rng.integers(0, 20, 500)], 1)]).astype(np.float32)
+    for seed in (1, 2):
+        prop = api.Proposal(seed=seed)
+        got = prop.scores(g, torch.from_numpy(feat).cuda(), tensor=True).cpu().numpy().astype(np.int64)
+        w = oracle_weights(prop)
+        want = np.array([O.score(O.mlp_logit(w, list(map(float, f)))) for f in feat], dtype=np.int64)
+        w16 = [np.asarray(a, dtype=np.uint16) for a in prop.arrays16()]
+        f32 = [(a.astype(np.uint32) << 16).view(np.float32).astype(np.float64) for a in w16]
+        w1, b1, w2, b2, w3 = f32[0].reshape(64, 3), f32[1], f32[2].reshape(64, 64), f32[3], f32[4]
+        h1 = np.maximum(feat.astype(np.float64) @ w1.T + b1, 0.0)
+        h2 = np.maximum(h1 @ w2.T + b2, 0.0)
+        dz = (np.abs(h1) @ np.abs(w2).T) @ np.abs(w3) * 2.0 ** -8 + (np.abs(h2) @ np.abs(w3)) * 2.0 ** -18
+        bound = np.floor(512 * dz) + 1
+        diff = np.abs(got - want)
+        assert np.all(diff <= bound), (diff.max(), bound[diff.argmax()])
+        assert got.min() >= 1 and got.max() <= 4097
+        # the tensor path reads the BF16-rounded hidden layer: its exact logits are closer still
+        zr = (np.maximum(_bf16_round(h1) @ w2.T + b2, 0.0) @ w3 + f32[5][0])
+        ar = 1 + np.floor(4096 * np.clip(zr / 8 + 0.5, 0, 1))
+        assert np.all(np.abs(got - ar) <= 1 + np.floor(512 * (np.abs(h2) @ np.abs(w3)) * 2.0 ** -18) + 1)
+
+
+def test_tensor_core_learned_sampler_is_unbiased():
+    """Any positive scores keep the estimator unbiased: the tensor-core learned
+    sampler's mean over 2^20 samples lies within 5 standard errors of the
+    exact count, and each sample's weight is A / a_x times the uniform steps."""
+    rp, col = G.erdos_renyi(300, 0.12, seed=6)
+    g = api.Graph(rp.cuda(), col.cuda())
+    og = O.Graph(*G.to_numpy(rp, col))
+    for name in ("4-clique", "house"):
+        k, edges = G.pattern(name)
+        exact = O.exact_count(og, O.plan(k, edges))
+        prop = api.Proposal(seed=3)
+        N = 1 << 20
+        s = g.sample_sums(name, seed=7, first=0, count=N, mlp=prop, mlp_tensor=1)
+        mu = s.sum / s.n
+        var = max(s.sumsq / s.n - mu * mu, 0.0)
+        assert abs(mu - exact) < 5 * math.sqrt(var / N), (name, mu, exact)
+        tr = g.trace(name, seed=7, first=0, count=4096, mlp=prop, mlp_tensor=1)
+        hit = tr["hit"] == 1
+        w = tr["factor"][:, 0].astype(np.float64)
+        for j in range(2, k):
+            learned = tr["aux"][:, j] > 0
+            fj = tr["factor"][:, j].astype(np.float64)
+            w = w * np.where(learned, fj / np.maximum(tr["aux"][:, j], 1), fj)
+        assert np.allclose(tr["w_f64"][hit], w[hit], rtol=1e-12)
+        assert hit.sum() > 0 and (tr["aux"][hit, 2] > 0).any()
