@@ -168,18 +168,27 @@ def kernel_source_hash():
 
 
 def ncu_traffic(config):
-    """Per-launch DRAM traffic of the sampler, scaled to one full launch of this
-    workload, from the committed ncu summary, if it was taken on the current
-    kernel sources."""
+    """DRAM bytes per sample of the sampler for each pattern (one-launch ncu
+    captures on this workload), from the committed ncu summary, if it was
+    taken on the current kernel sources; None otherwise."""
     summ = os.path.join(ROOT, "profiles", "ns_batch_kernel_%s.md" % config)
     if not os.path.exists(summ):
         return None
     txt = open(summ).read()
     m1 = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
-    m2 = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.e+]+)", txt)
-    if not (m1 and m2) or m1.group(1) != kernel_source_hash():
+    if not m1 or m1.group(1) != kernel_source_hash():
         return None
-    return float(m2.group(1))
+    per = {m.group(1): float(m.group(2))
+           for m in re.finditer(r"traffic_bytes_per_sample\[([^\]]+)\]:\s*([0-9.e+]+)", txt)}
+    return per or None
+
+
+def device_bytes_per_sample(g, patterns, count=1 << 18):
+    """Mean algorithmic bytes per sample of each batched job's stream (slot =
+    job index), from the device's per-sample sector counts (the oracle's
+    definition, parity-tested against it)."""
+    return {p: 32.0 * float(g.trace(p, seed=1, first=0, count=count, slot=q)["sectors"].astype("float64").mean())
+            for q, p in enumerate(patterns)}
 
 
 # ------------------------------------------------------------------ CPU oracle (cpu_baseline / reference arm)
@@ -344,9 +353,11 @@ def learned_vs_plain(g, api, patterns, n_max, selector=None, seed=5):
         (loss, rows), train_s = _timed(lambda: prop.train(g, name, seed=11, samples=1 << 20, epochs=3, batch=8192,
                                                           lr=3e-3))
         row = {"train_s": train_s, "train_rows": rows, "train_loss": loss}
-        for variant in ("plain", "learned"):
-            kw = {"mlp": prop} if variant == "learned" else {}
-            sch = api.NS_LEARNED if variant == "learned" else api.NS
+        for variant in ("plain", "learned", "learned_tc"):
+            kw = {} if variant == "plain" else {"mlp": prop}
+            if variant == "learned_tc":
+                kw["mlp_tensor"] = 1
+            sch = api.NS if variant == "plain" else api.NS_LEARNED
             r, t = _timed(lambda: g.estimate(name, scheme=sch, eps=EPS, delta=DELTA, seed=seed, window=WINDOW,
                                              n_max=n_max, max_seconds=60.0, **kw))
             row[variant] = _run_row(r, t)
@@ -362,8 +373,10 @@ def learned_vs_plain(g, api, patterns, n_max, selector=None, seed=5):
             row[label] = _run_row(r, t)
             row[label]["engine"] = "GS" if r["scheme_used"] == api.GS else "NS"
             row[label]["pilot_s"] = r["t_pilot_s"]
-        p, l = row["plain"], row["learned"]
-        row["learned_over_plain_time_per_sample"] = ((l["t_sample_s"] / max(l["samples"], 1))
+        p = row["plain"]
+        for v in ("learned", "learned_tc"):
+            l = row[v]
+            row[v + "_over_plain_time_per_sample"] = ((l["t_sample_s"] / max(l["samples"], 1))
                                                      / max(p["t_sample_s"] / max(p["samples"], 1), 1e-30))
         out[name] = row
     return out
@@ -768,23 +781,19 @@ def headline(args, wl):
             "e2e": e2e, "gpu_launches": int(launches), "clocks": ck, "learned_vs_plain": learned}
 
     peak, peak_kind = measured_peaks()
-    roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
-            "traffic": ncu_traffic(args.config), "kernel": "ns_batch_kernel<INTERSECT, compact>",
-            "peak_kind": peak_kind}
-    if world == 1 and not args.no_cpu_baseline:
-        og = oracle_graph(rp_np, col_np)
-        ores, owall, cores = oracle_sample(og, patterns, args.cpu_seconds)
-        cpu_n = sum(v["n"] for v in ores.values())
-        line["cpu_baseline"] = {"value": cpu_n / owall, "unit": "samples/s", "cores": cores, "kind": "oracle",
-                                "sample": "%d samples (prefix of each pattern's seed-1 stream, %s) split over %d "
-                                          "threads" % (cpu_n, "+".join(patterns), cores)}
-        # algorithmic bytes per sample from the oracle's per-sample accounting
-        bbar = {p: ores[p]["bytes"] / ores[p]["n"] for p in patterns}
+    kname = "ns_batch_kernel<INTERSECT_SINGLE, compact> then <INTERSECT, compact>" if any(
+        p in ("4-cycle", "house", "5-path") for p in patterns) else "ns_batch_kernel<INTERSECT, compact>"
+    roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None,
+            "kernel": kname, "peak_kind": peak_kind}
+    if world == 1:
+        # algorithmic bytes: per-sample sector counts of the device's traces
+        bbar = device_bytes_per_sample(g, patterns)
         algo_bytes = sum(bbar[p] * r[p]["samples"] for r in per_step for p in patterns)
         achieved = algo_bytes / kernel_s / 1e9
         roof.update({"achieved": achieved, "frac": achieved / peak if peak else None,
-                     "bytes_per_sample": bbar, "bytes_source": "oracle prefix sample", "launches": int(rounds),
-                     "avg_launch_ms": 1e3 * kernel_s / max(1, rounds)})
+                     "bytes_per_sample": bbar,
+                     "bytes_source": "device trace sector counts, 2^18 samples per pattern (the oracle's definition)",
+                     "launches": int(rounds), "avg_launch_ms": 1e3 * kernel_s / max(1, rounds)})
         # the random-access roofline of the same pattern: dependent chains of 32-byte
         # sector reads over a buffer the size of the CSR (secondary to the copy peak)
         gather = {"buffer_bytes": csr_bytes}
@@ -793,6 +802,19 @@ def headline(args, wl):
             gather["chain%d_GBps" % chain] = r_rand
             gather["frac_chain%d" % chain] = achieved / r_rand
         roof["gather_roofline"] = gather
+        tr = ncu_traffic(args.config)
+        if tr and all(p in tr for p in patterns):
+            roof["traffic"] = sum(tr[p] * r[p]["samples"] for r in per_step for p in patterns) / max(1, rounds)
+            roof["traffic_per_sample"] = tr
+    if world == 1 and not args.no_cpu_baseline:
+        og = oracle_graph(rp_np, col_np)
+        ores, owall, cores = oracle_sample(og, patterns, args.cpu_seconds)
+        cpu_n = sum(v["n"] for v in ores.values())
+        line["cpu_baseline"] = {"value": cpu_n / owall, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                                "sample": "%d samples (prefix of each pattern's seed-1 stream, %s) split over %d "
+                                          "threads" % (cpu_n, "+".join(patterns), cores)}
+        # the oracle's own byte count on its prefix: a cross-check of the device's
+        roof["bytes_per_sample_oracle_prefix"] = {p: ores[p]["bytes"] / ores[p]["n"] for p in patterns}
         if args.config == "rmat22":
             # the oracle's own time to converge, Algorithm 3 on every host core
             line["cpu_time_to_converge"] = {p: oracle_online_parallel(og, p, EPS, DELTA, 1, WINDOW, n_max, 300.0)

@@ -781,6 +781,37 @@ int og_ns_run(const og_graph *g, const og_plan *p, int mode, const og_mlp *mlp,
     return 0;
 }
 
+/* Mean and M2 (sum of squared deviations) of samples [first, first+count) by
+ * Welford's update in sample order (Welford 1962): the numerically stable
+ * counterpart of Algorithm 3's running sum and squared sum, for the
+ * cross-check var = sumsq / n - mu^2 = M2 / n. */
+int og_welford_run(const og_graph *g, const og_plan *p, int mode, const og_mlp *mlp,
+                   uint64_t seed, uint32_t slot, uint64_t first, uint64_t count, double *mean, double *m2)
+{
+    uint64_t md = (og_maxdeg(g) + 1) * OG_MAXK;
+    uint32_t *buf = (uint32_t *)malloc(sizeof(uint32_t) * md);
+    uint32_t *buf2 = (uint32_t *)malloc(sizeof(uint32_t) * md);
+    if (!buf || !buf2) { free(buf); free(buf2); return -1; }
+    double mu = 0.0, q = 0.0;
+    uint64_t n = 0;
+    for (uint64_t s = first; s < first + count; s++) {
+        uint64_t r[OG_MAXK];
+        for (int t = 0; t + 1 < p->k; t++) r[t] = og_choice_word(seed, s, slot, 0, (uint32_t)t);
+        og_record rec;
+        og_sample(g, p, r, mode, mlp, buf, buf2, &rec);
+        double x = rec.hit ? rec.w_f64 : 0.0;
+        n++;
+        double d = x - mu;
+        mu += d / (double)n;
+        q += d * (x - mu);
+    }
+    free(buf);
+    free(buf2);
+    *mean = mu;
+    *m2 = q;
+    return 0;
+}
+
 /* Per-sample algorithmic bytes of samples [first, first+count) into out. */
 int og_ns_bytes(const og_graph *g, const og_plan *p, int mode, const og_mlp *mlp,
                 uint64_t seed, uint32_t slot, uint64_t first, uint64_t count, double *out)

@@ -120,6 +120,8 @@ def lib():
             L.og_ns_run.restype = i32
             L.og_ns_run.argtypes = [C.c_void_p, P(Plan), i32, P(MLP16), u64, u32, u64, u64,
                                     P(Sums), C.c_void_p, i32]
+            L.og_welford_run.restype = i32
+            L.og_welford_run.argtypes = [C.c_void_p, P(Plan), i32, P(MLP16), u64, u32, u64, u64, P(dbl), P(dbl)]
             L.og_ns_bytes.restype = i32
             L.og_ns_bytes.argtypes = [C.c_void_p, P(Plan), i32, P(MLP16), u64, u32, u64, u64, C.c_void_p]
             L.og_phi_inv.restype = dbl
@@ -269,6 +271,16 @@ def ns_run(g, p, seed, first, count, mode=INTERSECT, mlp=None, slot=0, trace=Fal
     if rc != 0:
         raise MemoryError("oracle run failed")
     return acc, recs
+
+
+def welford(g, p, seed, first, count, mode=INTERSECT, mlp=None, slot=0):
+    """(mean, M2) of samples [first, first+count) by Welford's update."""
+    mu, m2 = C.c_double(), C.c_double()
+    rc = lib().og_welford_run(g.h, C.byref(p), mode, C.byref(mlp.c) if mlp else None, seed, slot, first, count,
+                              C.byref(mu), C.byref(m2))
+    if rc != 0:
+        raise MemoryError("oracle run failed")
+    return mu.value, m2.value
 
 
 def ns_bytes(g, p, seed, first, count, mode=INTERSECT, mlp=None, slot=0):

@@ -16,6 +16,7 @@
 // H1 = relu(X W1^T + b1) and A2 = H1 W2^T + b2 in shared memory, the output
 // and its gradient per row, and accumulates the weight gradients as small
 // tile contractions; per-block partials are summed in block order.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -302,15 +303,13 @@ __global__ void adam_step(float *w, const float *__restrict__ g, float *m, float
     v[i] = vi;
     const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + epsa);
     w[i] = wi;
-    const uint32_t bits = __float_as_uint(wi);
-    w16[i] = (uint16_t)((bits + 0x7FFFu + ((bits >> 16) & 1u)) >> 16);
+    w16[i] = __bfloat16_as_ushort(__float2bfloat16_rn(wi));   // nearest even; NaN stays NaN
 }
 
 __global__ void to_bf16(const float *__restrict__ w, uint16_t *w16) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= kGradFloats) return;
-    const uint32_t bits = __float_as_uint(w[i]);
-    w16[i] = (uint16_t)((bits + 0x7FFFu + ((bits >> 16) & 1u)) >> 16);
+    w16[i] = __bfloat16_as_ushort(__float2bfloat16_rn(w[i]));
 }
 
 static gpm_status cuda_fail(const char *where, cudaError_t e) {

@@ -237,3 +237,42 @@ def test_tensor_core_learned_sampler_is_unbiased():
             w = w * np.where(learned, fj / np.maximum(tr["aux"][:, j], 1), fj)
         assert np.allclose(tr["w_f64"][hit], w[hit], rtol=1e-12)
         assert hit.sum() > 0 and (tr["aux"][hit, 2] > 0).any()
+
+
+def test_one_adam_step_matches_the_host_step():
+    """One training step on one full batch is Adam's first step written out on
+    the host: m = 0.1 g, v = 0.001 g^2, w -= lr (m / 0.1) / (sqrt(v / 0.001) + 1e-8),
+    with g the mean-loss gradient at the starting weights (gpm_mlp_loss_grad)."""
+    rp, col = G.complete(5)
+    g = api.Graph(rp.cuda(), col.cuda())
+    rng = np.random.default_rng(8)
+    feat = torch.from_numpy(rng.uniform(0, 12, (500, 3)).astype(np.float32)).cuda()
+    label = torch.from_numpy((rng.random(500) < 0.3).astype(np.float32)).cuda()
+    prop = api.Proposal(seed=6)
+    w0 = prop.w32.clone()
+    _, grad = prop.loss_grad(g, feat, label)
+    lr = 1e-2
+    prop.train_rows(g, feat, label, epochs=1, batch=500, lr=lr)
+    gg = grad.double().cpu().numpy()
+    m, v = 0.1 * gg, 0.001 * gg * gg
+    want = w0.double().cpu().numpy() - lr * (m / 0.1) / (np.sqrt(v / 0.001) + 1e-8)
+    got = prop.w32.double().cpu().numpy()
+    assert np.allclose(got, want, rtol=2e-6, atol=1e-9)
+    # the BF16 copies are the FP32 weights rounded to nearest even
+    bits = prop.w32.cpu().numpy().view(np.uint32).astype(np.uint64)
+    rne = ((bits + 0x7FFF + ((bits >> 16) & 1)) >> 16).astype(np.uint16)
+    assert np.array_equal(prop.w16.cpu().numpy().view(np.uint16), rne)
+
+
+def test_bf16_copies_keep_nan():
+    """A NaN weight (here the output bias) makes every gradient and weight NaN;
+    the BF16 copies must be NaN too, not infinities or zeros."""
+    rp, col = G.complete(5)
+    g = api.Graph(rp.cuda(), col.cuda())
+    feat = torch.ones((64, 3), dtype=torch.float32, device="cuda")
+    label = torch.zeros(64, dtype=torch.float32, device="cuda")
+    prop = api.Proposal(seed=6)
+    prop.w32[4480] = float("nan")
+    prop.train_rows(g, feat, label, epochs=1, batch=64, lr=1e-2)
+    w16 = prop.w16.cpu().numpy().view(np.uint16).astype(np.uint32)
+    assert np.all((w16 & 0x7F80) == 0x7F80) and np.all((w16 & 0x7F) != 0)

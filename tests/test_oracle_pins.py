@@ -660,3 +660,41 @@ def test_lazy_union_order_and_closure_on_a_path():
     assert [rec.vert[i] for i in range(4)] == [1, 2, 3, 2] and rec.factor[3] == 2 and rec.hit == 0
     rec = O.sample(g, p, [_ceil_word(2, 6), _ceil_word(1, 2), _ceil_word(0, 2)], mode=O.LAZY)
     assert [rec.vert[i] for i in range(4)] == [1, 2, 3, 0] and rec.hit == 0    # 3-0 is not an edge
+
+
+# ------------------------------------------------------------------ variance: sums against Welford
+@pytest.mark.parametrize("name,induced,gen", [
+    ("5-path", False, ("rmat", 12)),          # hit rate near 1: the smallest CV^2 of the workloads
+    ("4-clique", False, ("rmat", 12)),
+    ("triangle", False, ("er", 0)),
+    ("wedge", False, ("complete", 9)),        # every sample hits with the same weight: var = 0
+])
+def test_sum_of_squares_variance_agrees_with_welford(name, induced, gen):
+    """Algorithm 3 keeps sum X and sum X^2; var = sumsq / n - mu^2 cancels when
+    CV^2 = var / mu^2 is small.  Its relative error is about
+    eps_mach (1 + 1 / CV^2) n; Welford's update (M2 / n) does not cancel.  On the
+    workloads' patterns the two agree within 1e-9 relative, and CV^2 stays far
+    from the regime where they would not."""
+    if gen[0] == "rmat":
+        rp, col = G.rmat(gen[1], 16, seed=2)
+    elif gen[0] == "er":
+        rp, col = G.erdos_renyi(3000, 0.01, seed=2)
+    else:
+        rp, col = G.complete(gen[1])
+    g = og(rp, col)
+    k, edges = G.pattern(name)
+    p = O.plan(k, edges, induced)
+    N = 200_000
+    acc, _ = O.ns_run(g, p, seed=3, first=0, count=N)
+    mu_w, m2 = O.welford(g, p, seed=3, first=0, count=N)
+    mu = acc.sum / N
+    var_s = max(acc.sumsq / N - mu * mu, 0.0)
+    var_w = m2 / N
+    assert mu == pytest.approx(mu_w, rel=1e-12)
+    if var_w == 0.0:
+        assert var_s <= 1e-12 * mu * mu
+        return
+    cv2 = var_w / (mu_w * mu_w)
+    assert abs(var_s - var_w) <= 1e-9 * var_w, (var_s, var_w, cv2)
+    # the cancellation bound predicts this agreement: eps (1 + 1/CV^2) log2(N) is far below 1e-9
+    assert 2.0 ** -52 * (1 + 1 / cv2) * math.log2(N) < 1e-9, cv2
