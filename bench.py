@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--config", default="rmat27", choices=list(WORKLOADS) + COMPANIONS,
                     help="workload; rmat27 (default) and rmat22 print the bench line, the others one JSON line "
                          "each for the companion workloads")
-    ap.add_argument("--ncu-case", default=None, choices=["4-clique", "5-clique", "4-cycle"],
+    ap.add_argument("--ncu-case", default=None,
+                    choices=["4-clique", "5-clique", "4-cycle", "diamond-induced", "4-path-induced"],
                     help="profiling case: the --config R-MAT graph resident, --warmup + --steps one-round "
                          "estimates (one sampler launch of one window each)")
     return ap.parse_args()
@@ -624,13 +625,17 @@ def ncu_case(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2405_03488_gb300 import api
+    from paper_2405_03488_gb300 import graphs as G
     wl = WORKLOADS[args.config if args.config in WORKLOADS else "rmat22"]
     rp, col = make_graph(wl, "cuda")
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     g = api.Graph(rp, col)
+    name = args.ncu_case.replace("-induced", "")
+    k, edges = G.pattern(name)
+    pat = (k, edges, args.ncu_case.endswith("-induced"))
     for s in range(args.warmup + args.steps):
-        g.estimate(args.ncu_case, eps=EPS, delta=DELTA, seed=1 + s, window=WINDOW, n_max=WINDOW)
+        g.estimate(pat, eps=EPS, delta=DELTA, seed=1 + s, window=WINDOW, n_max=WINDOW)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": args.ncu_case, "config": args.config, "launches": args.warmup + args.steps,
                       "window": WINDOW}))

@@ -271,10 +271,13 @@ gpm_status gpm_estimate_batch(gpm_graph *g, uint32_t count, const gpm_pattern *p
                               const double *eps, double delta, uint64_t seed, const gpm_config *cfg,
                               gpm_result *out);
 
-/* Times one convergence round of the batch under each candidate launch shape
- * (4 or 8 warps per block; on-chip candidate buffers of 256 or 512 entries per
- * warp, or the largest that keeps 4 blocks resident per SM) and writes the
- * fastest into io->block_warps and io->cap.
+/* Times three convergence rounds of the batch under each candidate launch
+ * shape (4 or 8 warps per block; on-chip candidate buffers of 256 or 512
+ * entries per warp, or the default) and writes the fastest into
+ * io->block_warps and io->cap; the default shape (8 warps, default buffers)
+ * is kept unless another is more than 2% faster.  The paper has no
+ * counterpart (its windows run on CPU threads, Sec. 5.4); library
+ * convenience for batched launches.
  * Estimates do not depend on the shape: samples are grouped in fixed chunks of
  * 64 whose partials are reduced in chunk order. */
 gpm_status gpm_autotune(gpm_graph *g, uint32_t count, const gpm_pattern *patterns, uint64_t seed, gpm_config *io);
@@ -379,11 +382,17 @@ gpm_status gpm_window_update(gpm_window *w, const gpm_sums *window, double z, do
 gpm_status gpm_sample_sums_static(gpm_graph *g, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
                                   uint64_t count, const gpm_config *cfg, gpm_sums *out);
 
-/* Per-sample records of samples [first, first + count) into HOST memory. */
+/* Per-sample records of samples [first, first + count) into HOST memory: the
+ * path each sample of Algorithm 4 / Lemma 1 takes (Sec. 4.2): the first-edge
+ * count M, every |S_j|, the matched vertices, the hit flag and the weight
+ * M prod |S_j| (0 on a miss), plus the algorithmic sectors of the path.  Used
+ * for parity checks and as the learned proposal's training traces. */
 gpm_status gpm_trace(gpm_graph *g, const gpm_pattern *pattern, uint64_t seed, uint64_t first,
                      uint64_t count, const gpm_config *cfg, gpm_sample_record *out);
 
-/* Exact count of the pattern (the plan's nested loops over every branch). */
+/* Exact count of the pattern: the plan's nested loops over every branch of
+ * the candidate sets (the exact GPM count C of Sec. 2.1 that GS runs on the
+ * sparsified graph, Sec. 2.2.2 / Algorithm 2; here on the whole graph). */
 gpm_status gpm_exact_count(gpm_graph *g, const gpm_pattern *pattern, uint64_t *out);
 
 /* ---- learned proposal (not in the paper; see gpm_scheme GPM_NS_LEARNED) ----
@@ -469,20 +478,26 @@ gpm_status gpm_sparsify_edges(gpm_graph *g, double p, uint64_t seed, uint32_t co
 gpm_status gpm_gather_probe(uint64_t bytes, uint32_t chain, uint64_t hops, double *sectors_bytes_per_s);
 
 /* Ask a running estimate on this handle to stop at its next round boundary
- * (it returns GPM_ERR_ABORTED with the partial result). */
+ * (it returns GPM_ERR_ABORTED with the partial result).  Library
+ * convenience: the paper has no counterpart.  Safe to call from another host
+ * thread while the estimate runs. */
 gpm_status gpm_abort(gpm_graph *g);
 
 /* Matching order and symmetry-breaking restrictions of a pattern (for
- * inspection): order[j] = pattern vertex at position j; restriction r reads
+ * inspection; the pruning of Sec. 4.2: matching order and symmetry breaking,
+ * which Algorithm 4 shows for the 4-cycle): order[j] = pattern vertex at
+ * position j; restriction r reads
  * v[res_lo[r]] < v[res_hi[r]]; *oriented = 1 if the first edge is drawn from
  * the m oriented edges.  Arrays hold GPM_MAX_K and 64 entries. */
 gpm_status gpm_plan(const gpm_pattern *pattern, int32_t *order, int32_t *res_lo, int32_t *res_hi,
                     int32_t *nres, int32_t *oriented);
 
-/* Phi^-1(p), the standard normal quantile used for z. */
+/* Phi^-1(p), the standard normal quantile of Eq. equ:error (z = Phi^-1(1 - delta/2)). */
 double gpm_normal_quantile(double p);
 
+/* The calling thread's message for the last failed call (library convenience). */
 const char *gpm_last_error(void);
+/* Library version string (library convenience). */
 const char *gpm_version(void);
 
 #ifdef __cplusplus

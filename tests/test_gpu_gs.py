@@ -77,16 +77,28 @@ def test_hybrid_returns_a_consistent_engine_result():
     g, og = pair(rp, col)
     r = g.estimate("triangle", scheme=api.HYBRID, eps=0.05, delta=0.01, seed=3, window=1 << 16)
     assert r["scheme_used"] in (api.NS, api.GS) and r["t_pilot_s"] > 0
-    if r["scheme_used"] == api.NS:
-        assert r["converged"] == 1 and r["eps_hat"] <= 0.05
-    else:
-        est, _ = O.gs_estimate(og, O.plan(*G.pattern("triangle")), 8, seed=3)
-        assert r["estimate"] == est
+    check_engine_result(r, og, "triangle", 8)
     rp, col = G.chung_lu(20000, n_cliques=20, clique_size=10, seed=5)
-    g = api.Graph(rp.cuda(), col.cuda())
-    r = g.estimate("7-clique", scheme=api.HYBRID, eps=0.05, delta=0.01, seed=3, window=1 << 16,
+    g, og = pair(rp, col)
+    r = g.estimate("6-clique", scheme=api.HYBRID, eps=0.05, delta=0.01, seed=3, window=1 << 16,
                    n_max=1 << 22, colors=2)
-    assert r["scheme_used"] in (api.NS, api.GS)
+    check_engine_result(r, og, "6-clique", 2)
+
+
+def check_engine_result(r, og, name, colors):
+    """Whichever engine the hybrid chose, its result is that engine's own: the
+    oracle's online NS run (same seed and window) or its GS estimate."""
+    k, edges = G.pattern(name)
+    assert r["scheme_used"] in (api.NS, api.GS) and r["t_pilot_s"] > 0
+    if r["scheme_used"] == api.NS:
+        o = O.ns_online(og, O.plan(k, edges), 0.05, 0.01, seed=3, window=1 << 16, n_max=1 << 22)
+        assert r["converged"] == o.converged
+        assert (r["samples"], r["hits"], r["rounds"]) == (o.samples, o.hits, o.rounds)
+        assert r["estimate"] == pytest.approx(o.estimate, rel=1e-12)
+        assert r["eps_hat"] == pytest.approx(o.eps_hat, rel=1e-10)
+    else:
+        est, _ = O.gs_estimate(og, O.plan(k, edges), colors, seed=3)
+        assert r["estimate"] == est
 
 
 def test_exact_count_deadline_returns_a_lower_bound():
