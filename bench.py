@@ -47,7 +47,7 @@ WORKLOADS = {
                "workload": "R-MAT scale 22, edge factor 16 (a,b,c = 0.57,0.19,0.19), 4-clique + 5-clique NS "
                            "eager-verify"},
 }
-COMPANIONS = ["er-triangle", "rmat24-batch", "chunglu-needle", "selector", "complex", "gs-variants"]
+COMPANIONS = ["er-triangle", "rmat24-batch", "chunglu-needle", "selector", "complex", "gs-variants", "profiler"]
 
 
 def parse():
@@ -596,6 +596,29 @@ def companion(args):
             out[name] = {"seconds": t, "estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"],
                          "hit_rate": r["hits"] / max(r["samples"], 1),
                          "samples_per_s": r["samples"] / max(r["t_sample_s"], 1e-12), "converged": r["converged"]}
+    elif args.config == "profiler":
+        # the two sample-count predictions against the samples the online run used
+        graphs = {"er-10k": G.erdos_renyi(10_000, 0.002, seed=1, device="cuda"),
+                  "rmat22": make_graph(WORKLOADS["rmat22"], "cuda")}
+        for gname, (rp, col) in graphs.items():
+            torch.cuda.synchronize()
+            g = api.Graph(rp, col)
+            pats = ["triangle", "4-cycle"] if gname == "er-10k" else ["triangle", "4-clique", "5-clique", "4-cycle"]
+            rowg = {}
+            for name in pats:
+                r, t = _timed(lambda: g.estimate(name, eps=EPS, delta=DELTA, seed=1, window=1 << 16,
+                                                 n_max=1 << 34, max_seconds=60.0))
+                pil = g.profile(name, kind="pilot", eps=EPS, delta=DELTA, seed=2)
+                spa = g.profile(name, kind="sparsified", frac=0.1, eps=EPS, delta=DELTA, seed=2)
+                rowg[name] = {"online_samples": r["samples"], "online_s": t,
+                              "pilot": {"n_s": pil["n_s"], "ratio": pil["n_s"] / max(r["samples"], 1),
+                                        "seconds": pil["seconds"], "samples_used": pil["samples_used"]},
+                              "sparsified_10pct": {"n_s": spa["n_s"], "ratio": spa["n_s"] / max(r["samples"], 1),
+                                                   "seconds": spa["seconds"], "samples_used": spa["samples_used"],
+                                                   "n_o": spa["n_o"], "eps_o": spa["eps_o"], "rho_g": spa["rho_g"],
+                                                   "rho_gp": spa["rho_gp"]}}
+            out[gname] = rowg
+            g.close()
     elif args.config == "gs-variants":
         # colour (c = 8) against Bernoulli edge (p = 1/8) sparsification, 8 samplers each, on R-MAT 16;
         # exact counts for reference

@@ -253,6 +253,31 @@ gpm_status gpm_estimate(gpm_graph *g, const gpm_pattern *pattern, gpm_scheme sch
 gpm_status gpm_hybrid_model(gpm_graph *g, const gpm_pattern *pattern, double eps, double delta, uint64_t seed,
                             const gpm_config *cfg, gpm_hybrid_info *out);
 
+/* Sample-count profilers (Sec. 5.3 and this library's pilot reading): the
+ * predicted number of NS samples N_s to reach eps at 1 - delta, the input of
+ * the NS cost model (Sec. 4.3).  kind GPM_PROFILE_PILOT: one window
+ * (cfg->window, default 2^20) of samples on G, N_s = (z sd / (eps mu))^2.
+ * kind GPM_PROFILE_SPARSIFIED: the paper's fast profiler: G' keeps each edge
+ * with probability frac (0.1 in the paper), NS-online on G' stops at a 50%
+ * error (windows of 2^14, at most 2^26 samples) after N_o samples with final
+ * predicted error eps_o, and N_s = N_o (eps_o / eps)^2 rho(G') / rho(G), rho
+ * the hit rates (rho(G) from 2^16 samples on G; the printed formula is not
+ * dimensionally consistent, see gpm_profile_info).  Neither changes any
+ * estimate. */
+#define GPM_PROFILE_PILOT 0
+#define GPM_PROFILE_SPARSIFIED 1
+typedef struct {
+    double n_s;             /* predicted samples (infinity when the profile saw no hit) */
+    double seconds;         /* wall time of the profile */
+    double n_o, eps_o;      /* sparsified: samples and final predicted error of the run on G' */
+    double rho_g, rho_gp;   /* hit rates on G and (sparsified) on G' */
+    uint64_t samples_used;  /* samples drawn by the profile on G and G' together */
+    int32_t kind, pad_;
+} gpm_profile_info;
+
+gpm_status gpm_profile(gpm_graph *g, const gpm_pattern *pattern, int32_t kind, double frac, double eps,
+                       double delta, uint64_t seed, const gpm_config *cfg, gpm_profile_info *out);
+
 /* Trains the MLP on given rows (DEVICE feat [rows][3], label [rows]): `epochs`
  * passes of Adam (lr; beta 0.9, 0.999) over minibatches of `batch` rows of the
  * mean cross-entropy on the logits; w32 (DEVICE, 4481) in/out, w16 (DEVICE,

@@ -58,6 +58,15 @@ class HybridInfo(C.Structure):
         return d
 
 
+class ProfileInfo(C.Structure):
+    _fields_ = [("n_s", C.c_double), ("seconds", C.c_double), ("n_o", C.c_double), ("eps_o", C.c_double),
+                ("rho_g", C.c_double), ("rho_gp", C.c_double), ("samples_used", C.c_uint64),
+                ("kind", C.c_int32), ("pad_", C.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad_"}
+
+
 class Result(C.Structure):
     _fields_ = [("estimate", C.c_double), ("ci_half_width", C.c_double), ("eps_hat", C.c_double),
                 ("sum", C.c_double), ("sumsq", C.c_double), ("samples", C.c_uint64),
@@ -106,6 +115,7 @@ SIGNATURES = [
     ("gpm_estimate_batch", _i32, [_V, _u32, P(Pattern), P(_dbl), _dbl, _u64, P(Config), P(Result)]),
     ("gpm_autotune", _i32, [_V, _u32, P(Pattern), _u64, P(Config)]),
     ("gpm_hybrid_model", _i32, [_V, P(Pattern), _dbl, _dbl, _u64, P(Config), P(HybridInfo)]),
+    ("gpm_profile", _i32, [_V, P(Pattern), _i32, _dbl, _dbl, _dbl, _u64, P(Config), P(ProfileInfo)]),
     ("gpm_mlp_train", _i32, [_V, _V, _V, _u64, _u32, _u32, C.c_float, _V, _V, P(_dbl)]),
     ("gpm_sample_sums", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), P(Sums)]),
     ("gpm_sample_sums_static", _i32, [_V, P(Pattern), _u64, _u64, _u64, P(Config), P(Sums)]),

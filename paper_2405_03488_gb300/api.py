@@ -142,6 +142,17 @@ class Graph:
               "gpm_hybrid_model")
         return info.as_dict()
 
+    def profile(self, pat, kind="pilot", frac=0.1, eps=0.01, delta=0.01, seed=1, **cfg):
+        """Predicted NS sample count: kind "pilot" (a window on G) or
+        "sparsified" (the paper's profiler on a frac-edge-sparsified G')."""
+        info = _lib.ProfileInfo()
+        pp = pattern(pat)
+        c = config(**cfg)
+        k = {"pilot": 0, "sparsified": 1}[kind]
+        check(_lib.load().gpm_profile(self.h, C.byref(pp), k, frac, eps, delta, seed, C.byref(c), C.byref(info)),
+              "gpm_profile")
+        return info.as_dict()
+
     def autotune(self, pats, seed=1, **cfg):
         """Fastest launch shape for these patterns: dict(block_warps, cap)."""
         arr = (_lib.Pattern * len(pats))(*[pattern(p) for p in pats])

@@ -970,6 +970,105 @@ static gpm_status hybrid_estimate(gpm_graph *h, const Plan &p, double eps, doubl
 
 }  // namespace gpm
 
+namespace gpm {
+
+// ------------------------------------------------------------------ sample-count profilers
+// Two predictions of N_s, the samples NS needs for eps at 1 - delta (the NS
+// cost model's input, Sec. 4.3), for comparison:
+//  PILOT (this library's reading): CV^2 = var / mu^2 from one window of
+//    samples on G itself, N_s = (z CV / eps)^2;
+//  SPARSIFIED (Sec. 5.3's fast profiler): G' keeps each edge of G with
+//    probability p (10% in the paper), NS-online runs on G' to an internal
+//    error of 50% at the same confidence and stops after N_o samples with a
+//    final predicted error eps_o; with per-sample CV^2 about 1 / rho for the
+//    hit rate rho, CV'^2 = N_o (eps_o / z)^2 on G' transfers to G as
+//    N_s = N_o (eps_o / eps)^2 rho(P, G') / rho(P, G), rho(P, G) from a short
+//    hit-rate run on G.  The printed formula has eps_o unsquared and the
+//    ratio of rho the other way round (neither is dimensionally consistent);
+//    this is the reading that is.
+gpm_status profile_samples(gpm_graph *h, const Plan &p, int kind, double frac, double eps, double delta,
+                           uint64_t seed, const gpm_config *cfg, gpm_profile_info *out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    std::memset(out, 0, sizeof(*out));
+    out->kind = kind;
+    const double z = normal_quantile(1.0 - delta / 2.0);
+    const uint32_t slot = cfg ? cfg->slot : 0;
+    if (kind == GPM_PROFILE_PILOT) {
+        const uint64_t Wp = (cfg && cfg->window) ? cfg->window : (1ull << 20);
+        gpm_status st = run_block(h, p, MODE_INTERSECT, seed ^ 0x9E3779B97F4A7C15ull, slot, 0, Wp, cfg, 0, nullptr,
+                                  nullptr);
+        if (st != GPM_OK) return st;
+        const Totals t = *h->totals_host;
+        const double mu = t.sum / (double)t.n;
+        const double var = std::max(0.0, t.sumsq / (double)t.n - mu * mu);
+        out->samples_used = t.n;
+        out->rho_g = (double)t.hits / (double)t.n;
+        out->n_s = mu > 0.0 ? z * z * var / (eps * eps * mu * mu) : INFINITY;
+    } else if (kind == GPM_PROFILE_SPARSIFIED) {
+        if (!(frac > 0.0 && frac <= 1.0)) {
+            set_error("gpm_profile: the sparsified profiler needs 0 < frac <= 1");
+            return GPM_ERR_ARG;
+        }
+        // G': every edge kept with probability frac (Algorithm 2's Bernoulli sampler)
+        const uint64_t t_keep = frac >= 1.0 ? (1ull << 32) : (uint64_t)std::floor(frac * 4294967296.0);
+        uint64_t *row = nullptr, kept = 0;
+        uint32_t *col = nullptr;
+        gpm_status st = sparsify_alloc(h, 1, seed ^ 0xD1B54A32D192ED03ull, 0, slot, &row, &col, &kept, nullptr,
+                                       nullptr, t_keep ? t_keep : 1);
+        if (st != GPM_OK) return st;
+        gpm_graph *gp = nullptr;
+        st = gpm_load_csr(h->d.n, row, col, GPM_DEVICE_PTRS, h->stream, &gp);
+        gpm_result r;
+        std::memset(&r, 0, sizeof(r));
+        if (st == GPM_OK) {
+            gpm_config c2;
+            std::memset(&c2, 0, sizeof(c2));
+            c2.window = 1ull << 14;
+            c2.n_max = 1ull << 26;
+            c2.slot = slot;
+            c2.max_seconds = cfg ? cfg->max_seconds : 0.0;
+            st = ns_estimate(gp, p, 0.5, delta, seed, &c2, &r);
+            if (st == GPM_ERR_NOT_CONVERGED) st = GPM_OK;
+        }
+        if (gp) gpm_free_graph(gp);
+        cudaFreeAsync(row, h->stream);
+        cudaFreeAsync(col, h->stream);
+        if (st != GPM_OK) return st;
+        out->samples_used = r.samples;
+        out->n_o = (double)r.samples;
+        out->eps_o = r.eps_hat;
+        out->rho_gp = r.samples ? (double)r.hits / (double)r.samples : 0.0;
+        // rho(P, G) from a short run on G
+        const uint64_t nh = 1ull << 16;
+        st = run_block(h, p, MODE_INTERSECT, seed ^ 0x5851F42D4C957F2Dull, slot, 0, nh, cfg, 0, nullptr, nullptr);
+        if (st != GPM_OK) return st;
+        out->samples_used += nh;
+        out->rho_g = (double)h->totals_host->hits / (double)h->totals_host->n;
+        out->n_s = (out->rho_g > 0.0 && r.converged && out->eps_o > 0.0)
+                       ? out->n_o * (out->eps_o / eps) * (out->eps_o / eps) * out->rho_gp / out->rho_g
+                       : INFINITY;
+    } else {
+        set_error("gpm_profile: unknown profiler kind");
+        return GPM_ERR_ARG;
+    }
+    out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return GPM_OK;
+}
+
+}  // namespace gpm
+
+extern "C" gpm_status gpm_profile(gpm_graph *h, const gpm_pattern *pattern, int32_t kind, double frac, double eps,
+                                  double delta, uint64_t seed, const gpm_config *cfg, gpm_profile_info *out) {
+    if (!h || !out || !(eps > 0.0) || !(delta > 0.0 && delta < 1.0)) {
+        set_error("gpm_profile: null argument, eps <= 0 or delta outside (0, 1)");
+        return GPM_ERR_ARG;
+    }
+    Plan p;
+    gpm_status st = plan_or_error(pattern, &p);
+    if (st != GPM_OK) return st;
+    return profile_samples(h, p, kind, frac, eps, delta, seed, cfg, out);
+}
+
 extern "C" gpm_status gpm_hybrid_model(gpm_graph *h, const gpm_pattern *pattern, double eps, double delta,
                                        uint64_t seed, const gpm_config *cfg, gpm_hybrid_info *out) {
     if (!h || !out) {

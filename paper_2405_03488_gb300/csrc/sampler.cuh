@@ -28,6 +28,7 @@ enum { MODE_INTERSECT = 0, MODE_CHECK = 1, MODE_LEARNED = 2, MODE_INTERSECT_SING
 #endif
 
 constexpr uint32_t kLearnedMax = 256;   // larger candidate sets are drawn uniformly
+constexpr uint32_t kLaneLookahead = 192; // learned lookahead: lists up to this long are walked by one lane
 // S_j = S_{j-1} cut by N(v_{j-1}): stream the list through on-chip searches
 // while |list| <= FACTOR * |usable part of S_{j-1}| + BIAS, else search the
 // list for each element of S_{j-1}

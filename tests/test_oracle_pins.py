@@ -698,3 +698,59 @@ def test_sum_of_squares_variance_agrees_with_welford(name, induced, gen):
     assert abs(var_s - var_w) <= 1e-9 * var_w, (var_s, var_w, cv2)
     # the cancellation bound predicts this agreement: eps (1 + 1/CV^2) log2(N) is far below 1e-9
     assert 2.0 ** -52 * (1 + 1 / cv2) * math.log2(N) < 1e-9, cv2
+
+
+# ------------------------------------------------------------------ GS variance model
+def test_gs_variance_model_equals_the_variance_over_every_colouring():
+    """The corrected variance model (oracle/gs_variance.py) against the exact
+    variance of C' c^(k-1) over all c^n colourings of a small graph."""
+    import itertools
+    from oracle import gs_variance
+    rp, col = G.random_small(8, 0.6, 31)
+    rp_n, col_n = G.to_numpy(rp, col)
+    g = og(rp, col)
+    for name, c in (("triangle", 2), ("4-clique", 2), ("4-cycle", 3), ("wedge", 2)):
+        k, edges = G.pattern(name)
+        p = O.plan(k, edges)
+        ms = brute.matches(rp_n, col_n, k, edges)
+        C = len(ms)
+        n = g.n
+        if c ** n > 7000:
+            continue
+        s1 = s2 = Fraction(0)
+        for cols in itertools.product(range(c), repeat=n):
+            row, cc = O.sparsify(g, np.array(cols, dtype=np.uint32))
+            x = Fraction(O.exact_count(O.Graph(row, cc), p) * c ** (k - 1))
+            s1 += x
+            s2 += x * x
+        N = c ** n
+        mean, var = s1 / N, s2 / N - (s1 / N) ** 2
+        assert mean == C
+        assert var == gs_variance.colour_variance(ms, k, c), name
+
+
+def test_gs_edge_variance_model_equals_the_variance_over_every_edge_subset():
+    """Bernoulli edge sparsification at p = 1/2: every subset of the m edges is
+    equally likely; the variance of C' 2^l over all of them equals the model."""
+    import itertools
+    from oracle import gs_variance
+    rp, col = G.random_small(7, 0.55, 12)
+    rp_n, col_n = G.to_numpy(rp, col)
+    edges_g = [(u, int(w)) for u in range(len(rp_n) - 1) for w in col_n[rp_n[u]:rp_n[u + 1]] if u < w]
+    m = len(edges_g)
+    assert m <= 14
+    for name in ("triangle", "4-cycle", "wedge"):
+        k, edges = G.pattern(name)
+        p = O.plan(k, edges)
+        ms = brute.matches(rp_n, col_n, k, edges)
+        l = len(edges)
+        s1 = s2 = Fraction(0)
+        for keep in itertools.product((0, 1), repeat=m):
+            kept = [e for e, b in zip(edges_g, keep) if b]
+            rr, cc = G.to_numpy(*G.from_edge_list(len(rp_n) - 1, kept))
+            x = Fraction(O.exact_count(O.Graph(rr, cc), p) * 2 ** l)
+            s1 += x
+            s2 += x * x
+        N = 2 ** m
+        assert s1 / N == len(ms)
+        assert s2 / N - (s1 / N) ** 2 == gs_variance.edge_variance(ms, l, Fraction(1, 2)), name
