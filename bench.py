@@ -47,7 +47,8 @@ WORKLOADS = {
                "workload": "R-MAT scale 22, edge factor 16 (a,b,c = 0.57,0.19,0.19), 4-clique + 5-clique NS "
                            "eager-verify"},
 }
-COMPANIONS = ["er-triangle", "rmat24-batch", "chunglu-needle", "selector", "complex", "gs-variants", "profiler"]
+COMPANIONS = ["er-triangle", "rmat24-batch", "chunglu-needle", "selector", "complex", "gs-variants", "profiler",
+              "nsbase"]
 
 
 def parse():
@@ -63,7 +64,8 @@ def parse():
                     help="workload; rmat27 (default) and rmat22 print the bench line, the others one JSON line "
                          "each for the companion workloads")
     ap.add_argument("--ncu-case", default=None,
-                    choices=["4-clique", "5-clique", "4-cycle", "diamond-induced", "4-path-induced"],
+                    choices=["4-clique", "5-clique", "4-cycle", "diamond-induced", "4-path-induced", "5-clique-learned",
+                             "4-cycle-learned", "5-clique-learned-tc"],
                     help="profiling case: the --config R-MAT graph resident, --warmup + --steps one-round "
                          "estimates (one sampler launch of one window each)")
     return ap.parse_args()
@@ -596,6 +598,30 @@ def companion(args):
             out[name] = {"seconds": t, "estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"],
                          "hit_rate": r["hits"] / max(r["samples"], 1),
                          "samples_per_s": r["samples"] / max(r["t_sample_s"], 1e-12), "converged": r["converged"]}
+    elif args.config == "nsbase":
+        # NS-base (lazy verify) against NS with eager verify, as in the paper's hit-rate and
+        # convergence comparisons: hit rate, per-sample CV^2, samples/s and time to +-1%
+        cases = [("rmat22", make_graph(WORKLOADS["rmat22"], "cuda"), ["4-clique", "5-clique", "4-cycle"]),
+                 ("er-10k", G.erdos_renyi(10_000, 0.002, seed=1, device="cuda"), ["triangle", "4-cycle"])]
+        for gname, (rp, col), pats in cases:
+            torch.cuda.synchronize()
+            g = api.Graph(rp, col)
+            rowg = {}
+            for name in pats:
+                row = {}
+                for label, verify in (("ns", "intersect"), ("ns_base", "lazy")):
+                    s_ = g.sample_sums(name, seed=9, first=0, count=1 << 22, verify=verify)
+                    mu = s_.sum / s_.n
+                    r, t = _timed(lambda: g.estimate(name, eps=EPS, delta=DELTA, seed=1, window=WINDOW,
+                                                     n_max=1 << 36, max_seconds=30.0, verify=verify))
+                    row[label] = {"hit_rate": s_.hits / s_.n,
+                                  "cv2": (s_.sumsq / s_.n - mu * mu) / (mu * mu) if mu > 0 else None,
+                                  "time_to_converge_s": t, "converged": bool(r["converged"]),
+                                  "samples": r["samples"], "eps_hat": r["eps_hat"], "estimate": r["estimate"],
+                                  "samples_per_s": r["samples"] / max(r["t_sample_s"], 1e-12)}
+                rowg[name] = row
+            out[gname] = rowg
+            g.close()
     elif args.config == "profiler":
         # the two sample-count predictions against the samples the online run used
         graphs = {"er-10k": G.erdos_renyi(10_000, 0.002, seed=1, device="cuda"),
@@ -654,11 +680,18 @@ def ncu_case(args):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     g = api.Graph(rp, col)
-    name = args.ncu_case.replace("-induced", "")
+    name = args.ncu_case.replace("-induced", "").replace("-learned", "").replace("-tc", "")
     k, edges = G.pattern(name)
     pat = (k, edges, args.ncu_case.endswith("-induced"))
+    kw = {}
+    if "-learned" in args.ncu_case:
+        prop = api.Proposal(seed=1)
+        prop.train(g, name, seed=11, samples=1 << 18, epochs=1, batch=8192, lr=3e-3)
+        kw = {"scheme": api.NS_LEARNED, "mlp": prop}
+        if args.ncu_case.endswith("-tc"):
+            kw["mlp_tensor"] = 1
     for s in range(args.warmup + args.steps):
-        g.estimate(pat, eps=EPS, delta=DELTA, seed=1 + s, window=WINDOW, n_max=WINDOW)
+        g.estimate(pat, eps=EPS, delta=DELTA, seed=1 + s, window=WINDOW, n_max=WINDOW, **kw)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": args.ncu_case, "config": args.config, "launches": args.warmup + args.steps,
                       "window": WINDOW}))

@@ -249,48 +249,15 @@ static __device__ __noinline__ uint32_t learned_pick(const DGraph &g, const Plan
         cu[i] = (uint32_t)(__ldg(g.up + x) - xb);
     }
     __syncwarp();
-    // lookahead sizes |S_{j+1}(x)| into cu.  When S_{j+1}(x) is S_j above x cut
-    // by N(x) (x itself the bound: cliques), a candidate whose list above x is
-    // short is counted by its own lane (its list walked, each entry searched in
-    // S_j above x on chip), so 32 candidates' list reads overlap; every other
-    // candidate gets one warp-wide count.
-    const int jj = j + 1;
-    bool lane_form = p.reuse[jj] == 1 && ((p.lower[jj] >> j) & 1u);
-    uint32_t lo_rest = 0;
-    for (int i = 0; i < j; i++)
-        if ((p.lower[jj] >> i) & 1u) lo_rest = wm.v[i] > lo_rest ? wm.v[i] : lo_rest;
-    for (uint32_t base = 0; base < sz; base += 32) {
-        const uint32_t i = base + lane;
-        bool mine = false;
-        if (lane_form && i < sz) {
-            const uint32_t L = cd[i] - cu[i];
-            mine = Sj[i] > lo_rest && L <= kLaneLookahead;
-        }
-        if (mine) {
-            const uint32_t *lst = g.col + cb[i] + cu[i];
-            const uint32_t L = cd[i] - cu[i], P = sz - i - 1;
-            const uint32_t *S = Sj + i + 1;
-            uint32_t cnt = 0;
-            uint32_t t = 0;
-            for (; t + 4 <= L; t += 4) {
-                const uint32_t y0 = __ldg(lst + t), y1 = __ldg(lst + t + 1), y2 = __ldg(lst + t + 2),
-                               y3 = __ldg(lst + t + 3);
-                cnt += lane_contains_shared(S, P, y0) + lane_contains_shared(S, P, y1) +
-                       lane_contains_shared(S, P, y2) + lane_contains_shared(S, P, y3);
-            }
-            for (; t < L; t++) cnt += lane_contains_shared(S, P, __ldg(lst + t));
-            cu[i] = cnt;
-        }
-        unsigned rest = __ballot_sync(kFull, i < sz && !mine);
-        while (rest) {
-            const uint32_t r = base + (uint32_t)(__ffs(rest) - 1);
-            rest &= rest - 1;
-            const uint64_t xb = cb[r], dx = cd[r];
-            const uint64_t nxt = lookahead_count(g, p, wm, Sj, sz, r, j, lb, le, xb, xb + dx, xb + cu[r]);
-            __syncwarp();
-            if (lane == 0) cu[r] = (uint32_t)nxt;
-            __syncwarp();
-        }
+    // lookahead sizes |S_{j+1}(x)|, one warp-wide count per candidate, into cu
+    // (lane-per-candidate forms of this count, walking each candidate's list
+    // in its own lane, measured no faster: the count's instructions, not the
+    // latency of the list reads, bound it)
+    for (uint32_t i = 0; i < sz; i++) {
+        const uint64_t xb = cb[i], dx = cd[i];
+        const uint64_t nxt = lookahead_count(g, p, wm, Sj, sz, i, j, lb, le, xb, xb + dx, xb + cu[i]);
+        __syncwarp();
+        if (lane == 0) cu[i] = (uint32_t)nxt;
     }
     __syncwarp();
     uint64_t A = 0;

@@ -28,7 +28,6 @@ enum { MODE_INTERSECT = 0, MODE_CHECK = 1, MODE_LEARNED = 2, MODE_INTERSECT_SING
 #endif
 
 constexpr uint32_t kLearnedMax = 256;   // larger candidate sets are drawn uniformly
-constexpr uint32_t kLaneLookahead = 192; // learned lookahead: lists up to this long are walked by one lane
 // S_j = S_{j-1} cut by N(v_{j-1}): stream the list through on-chip searches
 // while |list| <= FACTOR * |usable part of S_{j-1}| + BIAS, else search the
 // list for each element of S_{j-1}
@@ -58,6 +57,7 @@ struct RunArgs {
     gpm_sample_record *trace;     // optional per-sample records (device)
     uint32_t slot;
     uint32_t cap;                 // entries per on-chip candidate buffer
+    uint32_t cap2;                // entries of the third buffer (vertex-induced plans: a staged non-neighbour list)
     uint32_t chunk;               // samples per chunk
     uint32_t nchunks;
     uint32_t stride;              // chunks of the range between consecutive chunks of this launch
@@ -95,6 +95,13 @@ __device__ __forceinline__ void load_step_plan(const Plan &src, StepPlan *dst) {
 constexpr int kWarpHeaderWords = 88;
 constexpr int kTestSlots = 9;   // positions before the last of a 10-vertex pattern
 
+// Words per warp slice, rounded up to an even count so that every warp's
+// 8-byte fields (factors, test-table pointers, learned row starts) stay
+// 8-byte aligned for any buffer sizes.
+__host__ __device__ inline uint32_t warp_words(uint32_t cap, uint32_t cap2, bool learned) {
+    return (kWarpHeaderWords + 2 * cap + cap2 + (learned ? kLearnedWarpWords : 0) + 1u) & ~1u;
+}
+
 struct WarpMem {
     uint64_t *fac;
     uint32_t *v;
@@ -102,6 +109,7 @@ struct WarpMem {
     uint64_t *tptr;        // step-2 test table (see kWarpHeaderWords)
     uint32_t *tlen, *tneq;
     uint32_t *S0, *S1;
+    uint32_t *S2;          // vertex-induced plans: a non-neighbour list staged for the step's tests
     uint16_t *htile;       // learned, tensor cores: BF16 layer-1 outputs of 16 candidates
     uint32_t *score;       // learned: a_x of each candidate
     const float *W;        // learned: block copy of the weights (FP32, gpm_mlp order)
@@ -111,7 +119,7 @@ struct WarpMem {
 // Block-level setup: the learned weights (BF16 -> FP32, in the gpm_mlp order;
 // every lane reads the same weight at once, a broadcast) and each warp's slices.
 template <int MODE>
-__device__ __forceinline__ WarpMem warp_mem(uint64_t *smem64, uint32_t cap, const gpm_mlp &mlp) {
+__device__ __forceinline__ WarpMem warp_mem(uint64_t *smem64, uint32_t cap, const gpm_mlp &mlp, uint32_t cap2 = 0) {
     uint32_t *smem = reinterpret_cast<uint32_t *>(smem64);
     float *W = reinterpret_cast<float *>(smem);
     if (MODE == MODE_LEARNED) {
@@ -133,7 +141,7 @@ __device__ __forceinline__ WarpMem warp_mem(uint64_t *smem64, uint32_t cap, cons
         smem += kMlpSmemFloats;
     }
     const unsigned warp = threadIdx.x >> 5;
-    const uint32_t per = kWarpHeaderWords + 2 * cap + (MODE == MODE_LEARNED ? kLearnedWarpWords : 0);
+    const uint32_t per = warp_words(cap, cap2, MODE == MODE_LEARNED);
     uint32_t *base = smem + warp * per;
     WarpMem wm;
     wm.fac = reinterpret_cast<uint64_t *>(base);
@@ -144,8 +152,9 @@ __device__ __forceinline__ WarpMem warp_mem(uint64_t *smem64, uint32_t cap, cons
     wm.tneq = base + 79;
     wm.S0 = base + kWarpHeaderWords;
     wm.S1 = wm.S0 + cap;
-    wm.htile = reinterpret_cast<uint16_t *>(wm.S1 + cap);
-    wm.score = wm.S1 + cap + kHTileWords;
+    wm.S2 = wm.S1 + cap;
+    wm.htile = reinterpret_cast<uint16_t *>(wm.S2 + cap2);
+    wm.score = wm.S2 + cap2 + kHTileWords;
     wm.W = W;
     wm.W2b = reinterpret_cast<const uint16_t *>(W + 4482);
     return wm;
@@ -448,12 +457,25 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 const bool drop = p.reuse[j] == 2;
                 const uint32_t P = prev_size;
                 const uint32_t off = (has_lo && lo >= vj1) ? prev_off : 0u;
+                // the kept elements exceed the bound, so only N(v_{j-1}) above it
+                // is tested: staged on chip when it fits the third buffer
+                int n2 = -1;
+                if (!kCompact && drop && a.cap2) {   // the compact variant runs edge-induced plans only
+                    const uint64_t ds = above(j - 1, b, en);
+                    // staging pays when the list is not much longer than the elements tested
+                    if (en - ds <= a.cap2 && en - ds <= 4ull * (P - off) + 64) {
+                        for (uint64_t q = ds + lane; q < en; q += 32) wm.S2[q - ds] = __ldg(g.col + q);
+                        n2 = (int)(en - ds);
+                        __syncwarp();
+                    }
+                }
                 for (uint32_t base = off; base < P; base += 32) {
                     const uint32_t idx = base + lane;
                     const bool valid = idx < P;
                     const uint32_t y = valid ? Sp[idx] : 0u;
                     bool ok = valid && (!has_lo || y > lo) && y != vj1;
-                    if (drop) ok = ok && !lane_contains(g.col + b, en - b, y);
+                    if (drop) ok = ok && !(n2 >= 0 ? lane_contains_shared(wm.S2, (uint32_t)n2, y)
+                                                   : lane_contains(g.col + b, en - b, y));
                     const unsigned m = __ballot_sync(kFull, ok);
                     if (ok) Sc[count + __popc(m & lanemask_lt())] = y;
                     count += __popc(m);
@@ -505,10 +527,31 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 // it, and its vertex when y could equal it (a non-edge not
                 // below the bound y already exceeds; membership in N(v_i)
                 // rules out y = v_i, the graph having no loops)
+                // (vertex-induced) the shortest non-neighbour list, above the
+                // bound, staged in the third buffer when it fits
+                int neg_staged = -1;
+                uint32_t n2 = 0;
+                if (!kCompact && a.cap2 && p.induced && !empty) {
+                    const bool nb = (int)lane < j && !((back >> lane) & 1u);
+                    const uint64_t nkey = nb ? (((le - lb) << 5) | lane) : ~0ull;
+                    const uint64_t best = warp_min_u64(nkey);
+                    if (best != ~0ull) {
+                        const int q = (int)(best & 31u);
+                        const uint64_t qb = __shfl_sync(kFull, lb, q), qe = __shfl_sync(kFull, le, q);
+                        const uint64_t qs = above(q, qb, qe);
+                        if (qe - qs <= a.cap2 && qe - qs <= 4ull * (de - dstart) + 64) {
+                            for (uint64_t t = qs + lane; t < qe; t += 32) wm.S2[t - qs] = __ldg(g.col + t);
+                            n2 = (uint32_t)(qe - qs);
+                            neg_staged = q;
+                            __syncwarp();
+                        }
+                    }
+                }
                 {
                     const bool edge = (int)lane < j && ((back >> lane) & 1u);
                     const bool nonedge = (int)lane < j && !edge;
-                    const bool test = (edge && (int)lane != driver && (int)lane != staged) || (nonedge && p.induced);
+                    const bool test = (edge && (int)lane != driver && (int)lane != staged) ||
+                                      (nonedge && p.induced && (int)lane != neg_staged);
                     const bool neq = nonedge && !(has_lo && wm.v[lane] <= lo);
                     const unsigned tm = __ballot_sync(kFull, test), nm = __ballot_sync(kFull, neq);
                     if (test) {
@@ -525,6 +568,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                     bool ok = true;
                     for (int t = 0; t < nneq; t++) ok = ok && y != wm.tneq[t];
                     if (staged >= 0) ok = ok && lane_contains_shared(Sp, plen, y);
+                    if (neg_staged >= 0) ok = ok && !lane_contains_shared(wm.S2, n2, y);
                     for (int t = 0; t < ntest; t++) {
                         const uint32_t ln = wm.tlen[t];
                         ok = ok && (lane_contains(g.col + wm.tptr[t], ln & 0x7FFFFFFFu, y) != (ln >> 31));
@@ -736,10 +780,23 @@ inline int kernel_mode(int mode, bool single) {
 // ------------------------------------------------------------------ launch shape
 struct Shape {
     uint32_t blocks, warps, cap, chunk;
+    uint32_t cap2;   // third buffer (vertex-induced plans), 0 = none
 };
 
+// Vertex-induced plans in the uniform modes get a third buffer of up to 512
+// entries for a staged non-neighbour list (3 x 512 entries per warp still
+// leave room for 4 resident blocks of 8 warps).
+#ifndef GPM_THIRD_MAX
+#define GPM_THIRD_MAX 512
+#endif
+inline uint32_t third_buffer(int kmode, bool induced, uint32_t cap) {
+    const uint32_t c = cap < GPM_THIRD_MAX ? cap : GPM_THIRD_MAX;
+    return (induced && (kmode == MODE_INTERSECT || kmode == MODE_INTERSECT_SINGLE)) ? ((c + 1u) & ~1u) : 0;
+}
+
+
 inline size_t smem_bytes(const Shape &sh, int mode) {
-    const size_t per = kWarpHeaderWords + 2 * sh.cap + (mode == MODE_LEARNED ? kLearnedWarpWords : 0);
+    const size_t per = warp_words(sh.cap, sh.cap2, mode == MODE_LEARNED);
     return (size_t)sh.warps * per * sizeof(uint32_t) +
            (mode == MODE_LEARNED ? kMlpSmemFloats * sizeof(float) : 0);
 }
@@ -783,6 +840,7 @@ inline Shape pick_shape(gpm_graph *h, const gpm_config *cfg, uint64_t count) {
     sh.cap = (cfg && cfg->cap) ? cfg->cap : 0;   // 0: fit_cap at launch
     sh.blocks = (cfg && cfg->grid_blocks) ? cfg->grid_blocks : 0;
     sh.chunk = kChunk;
+    sh.cap2 = 0;
     return sh;
 }
 

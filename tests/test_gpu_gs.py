@@ -249,3 +249,22 @@ def test_pilot_sample_count_predicts_the_online_run(name, eps):
     r = g.estimate(name, eps=eps, delta=0.01, seed=3, window=1 << 14, n_max=1 << 32)
     assert r["converged"] == 1 and info["n_s"] > 8 * (1 << 14)
     assert 0.5 < r["samples"] / info["n_s"] < 2.0, (r["samples"], info["n_s"])
+
+
+@pytest.mark.parametrize("name,c", [("triangle", 2), ("4-cycle", 3)])
+def test_gs_sampler_variance_follows_the_corrected_model(name, c):
+    """The spread of R independent GPU colourings (the sample standard deviation
+    behind the R-sampler interval) against the corrected variance model of
+    the oracle (pairs of matches sharing z vertices add c^(z-1) - 1)."""
+    from oracle import brute, gs_variance
+    rp, col = G.erdos_renyi(22, 0.4, seed=6)
+    g, og = pair(rp, col)
+    k, edges = G.pattern(name)
+    ms = brute.matches(*G.to_numpy(rp, col), k, edges)
+    var_model = float(gs_variance.colour_variance(ms, k, c))
+    R, delta = 3000, 0.01
+    r = g.estimate(name, scheme=api.GS, seed=9, delta=delta, colors=c, samplers=R)
+    z = O.phi_inv(1 - delta / 2)
+    s2 = (r["ci_half_width"] * math.sqrt(R) / z) ** 2
+    assert abs(r["estimate"] - len(ms)) < 5 * math.sqrt(var_model / R)
+    assert s2 == pytest.approx(var_model, rel=0.2), (s2, var_model)

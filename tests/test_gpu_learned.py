@@ -265,8 +265,9 @@ def test_one_adam_step_matches_the_host_step():
 
 
 def test_bf16_copies_keep_nan():
-    """A NaN weight (here the output bias) makes every gradient and weight NaN;
-    the BF16 copies must be NaN too, not infinities or zeros."""
+    """A NaN weight (here the output bias) spreads NaN to every weight whose
+    gradient it reaches; the BF16 copies of those must be NaN too, not
+    infinities or zeros, and every finite weight keeps its nearest-even copy."""
     rp, col = G.complete(5)
     g = api.Graph(rp.cuda(), col.cuda())
     feat = torch.ones((64, 3), dtype=torch.float32, device="cuda")
@@ -274,5 +275,10 @@ def test_bf16_copies_keep_nan():
     prop = api.Proposal(seed=6)
     prop.w32[4480] = float("nan")
     prop.train_rows(g, feat, label, epochs=1, batch=64, lr=1e-2)
+    w32 = prop.w32.cpu().numpy()
     w16 = prop.w16.cpu().numpy().view(np.uint16).astype(np.uint32)
-    assert np.all((w16 & 0x7F80) == 0x7F80) and np.all((w16 & 0x7F) != 0)
+    nan = np.isnan(w32)
+    assert nan.sum() > 64
+    assert np.all((w16[nan] & 0x7F80) == 0x7F80) and np.all((w16[nan] & 0x7F) != 0)
+    bits = w32[~nan].view(np.uint32).astype(np.uint64)
+    assert np.array_equal(w16[~nan], ((bits + 0x7FFF + ((bits >> 16) & 1)) >> 16).astype(np.uint32))
