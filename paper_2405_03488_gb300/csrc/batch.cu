@@ -46,7 +46,7 @@ struct BatchCtl {
 struct BatchArgs {
     uint64_t seed, window;
     double z;
-    uint32_t njobs, cap, chunk, chunks_per_job, cap2;
+    uint32_t njobs, cap, chunk, chunks_per_job;
     gpm_mlp mlp;
     uint32_t mlp_tc;
 };
@@ -61,14 +61,13 @@ __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOC
     extern __shared__ __align__(16) uint64_t smem64[];
     __shared__ StepPlan splan[8];
     const unsigned lane = lane_id();
-    WarpMem wm = warp_mem<MODE>(smem64, ba.cap, ba.mlp, ba.cap2);
+    WarpMem wm = warp_mem<MODE>(smem64, ba.cap, ba.mlp);
     StepPlan *sp = &splan[threadIdx.x >> 5];
     uint32_t cur_job = 0xFFFFFFFFu;
     const uint32_t total = ctl->total_chunks;
     RunArgs a;
     a.seed = ba.seed;
     a.cap = ba.cap;
-    a.cap2 = ba.cap2;
     a.trace = nullptr;
     a.mlp_tc = ba.mlp_tc;
     for (;;) {
@@ -235,7 +234,6 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
     const bool compact = !induced && (kmode == MODE_INTERSECT || kmode == MODE_INTERSECT_SINGLE);
     if (sh.cap == 0) sh.cap = default_cap(h, kBatchStaticSmem, sh.warps, mode, induced);
     if (mode == MODE_LEARNED && sh.cap < kLearnedMax) sh.cap = kLearnedMax;
-    sh.cap2 = third_buffer(kmode, induced, sh.cap);
     const uint64_t cpj = (W + sh.chunk - 1) / sh.chunk;
     if (cpj * nj >= (1ull << 31)) {
         set_error("batch too large for one launch");
@@ -249,7 +247,6 @@ gpm_status batch_estimate(gpm_graph *h, const std::vector<Plan> &plans, const do
     ba.cap = sh.cap;
     ba.chunk = sh.chunk;
     ba.chunks_per_job = (uint32_t)cpj;
-    ba.cap2 = sh.cap2;
     std::memset(&ba.mlp, 0, sizeof(ba.mlp));
     if (mode == MODE_LEARNED) ba.mlp = *cfg->mlp;
     ba.mlp_tc = (mode == MODE_LEARNED && cfg->mlp_tensor) ? 1u : 0u;

@@ -126,7 +126,7 @@ template <int MODE, bool TRACE>
 __global__ void __launch_bounds__(256, (MODE == MODE_LEARNED) ? 2 : GPM_MIN_BLOCKS) ns_kernel(const DGraph g, const Plan p, const RunArgs a) {
     extern __shared__ __align__(16) uint64_t smem64[];
     const unsigned lane = lane_id();
-    WarpMem wm = warp_mem<MODE>(smem64, a.cap, a.mlp, a.cap2);
+    WarpMem wm = warp_mem<MODE>(smem64, a.cap, a.mlp);
     const uint64_t end = a.first + a.count;
     for (;;) {
         unsigned c = 0;
@@ -284,7 +284,6 @@ static gpm_status run_block(gpm_graph *h, const Plan &p, int mode, uint64_t seed
     Shape sh = pick_shape(h, cfg, count);
     if (sh.cap == 0) sh.cap = default_cap(h, 0, sh.warps, mode, p.induced);   // ns_kernel: no static shared memory
     if (mode == MODE_LEARNED && sh.cap < kLearnedMax) sh.cap = kLearnedMax;
-    sh.cap2 = third_buffer(kernel_mode(mode, plan_single_steps(p)), p.induced, sh.cap);
     const uint64_t all_chunks = (count + sh.chunk - 1) / sh.chunk;
     const uint64_t nchunks = (rank < all_chunks) ? (all_chunks - rank + world - 1) / world : 0;
     if (nchunks_out) *nchunks_out = nchunks;
@@ -305,7 +304,6 @@ static gpm_status run_block(gpm_graph *h, const Plan &p, int mode, uint64_t seed
     a.trace = trace;
     a.slot = slot;
     a.cap = sh.cap;
-    a.cap2 = sh.cap2;
     a.chunk = sh.chunk;
     a.nchunks = (uint32_t)nchunks;
     a.stride = world;
@@ -1212,7 +1210,6 @@ extern "C" gpm_status gpm_sample_sums_static(gpm_graph *h, const gpm_pattern *pa
     const int mode = mode_of(cfg);
     if (sh.cap == 0) sh.cap = default_cap(h, 0, sh.warps, mode, p.induced);
     if (mode == MODE_LEARNED && sh.cap < kLearnedMax) sh.cap = kLearnedMax;
-    sh.cap2 = third_buffer(kernel_mode(mode, plan_single_steps(p)), p.induced, sh.cap);
     const uint64_t nchunks = (count + sh.chunk - 1) / sh.chunk;   // <= kStaticMaxChunks
     RunArgs a;
     a.seed = seed;
@@ -1223,7 +1220,6 @@ extern "C" gpm_status gpm_sample_sums_static(gpm_graph *h, const gpm_pattern *pa
     a.trace = nullptr;
     a.slot = cfg ? cfg->slot : 0;
     a.cap = sh.cap;
-    a.cap2 = sh.cap2;
     a.chunk = sh.chunk;
     a.nchunks = (uint32_t)nchunks;
     a.stride = 1;

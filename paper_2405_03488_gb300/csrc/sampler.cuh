@@ -57,7 +57,6 @@ struct RunArgs {
     gpm_sample_record *trace;     // optional per-sample records (device)
     uint32_t slot;
     uint32_t cap;                 // entries per on-chip candidate buffer
-    uint32_t cap2;                // entries of the third buffer (vertex-induced plans: a staged non-neighbour list)
     uint32_t chunk;               // samples per chunk
     uint32_t nchunks;
     uint32_t stride;              // chunks of the range between consecutive chunks of this launch
@@ -98,8 +97,8 @@ constexpr int kTestSlots = 9;   // positions before the last of a 10-vertex patt
 // Words per warp slice, rounded up to an even count so that every warp's
 // 8-byte fields (factors, test-table pointers, learned row starts) stay
 // 8-byte aligned for any buffer sizes.
-__host__ __device__ inline uint32_t warp_words(uint32_t cap, uint32_t cap2, bool learned) {
-    return (kWarpHeaderWords + 2 * cap + cap2 + (learned ? kLearnedWarpWords : 0) + 1u) & ~1u;
+__host__ __device__ inline uint32_t warp_words(uint32_t cap, bool learned) {
+    return (kWarpHeaderWords + 2 * cap + (learned ? kLearnedWarpWords : 0) + 1u) & ~1u;
 }
 
 struct WarpMem {
@@ -109,7 +108,6 @@ struct WarpMem {
     uint64_t *tptr;        // step-2 test table (see kWarpHeaderWords)
     uint32_t *tlen, *tneq;
     uint32_t *S0, *S1;
-    uint32_t *S2;          // vertex-induced plans: a non-neighbour list staged for the step's tests
     uint16_t *htile;       // learned, tensor cores: BF16 layer-1 outputs of 16 candidates
     uint32_t *score;       // learned: a_x of each candidate
     const float *W;        // learned: block copy of the weights (FP32, gpm_mlp order)
@@ -119,7 +117,7 @@ struct WarpMem {
 // Block-level setup: the learned weights (BF16 -> FP32, in the gpm_mlp order;
 // every lane reads the same weight at once, a broadcast) and each warp's slices.
 template <int MODE>
-__device__ __forceinline__ WarpMem warp_mem(uint64_t *smem64, uint32_t cap, const gpm_mlp &mlp, uint32_t cap2 = 0) {
+__device__ __forceinline__ WarpMem warp_mem(uint64_t *smem64, uint32_t cap, const gpm_mlp &mlp) {
     uint32_t *smem = reinterpret_cast<uint32_t *>(smem64);
     float *W = reinterpret_cast<float *>(smem);
     if (MODE == MODE_LEARNED) {
@@ -141,7 +139,7 @@ __device__ __forceinline__ WarpMem warp_mem(uint64_t *smem64, uint32_t cap, cons
         smem += kMlpSmemFloats;
     }
     const unsigned warp = threadIdx.x >> 5;
-    const uint32_t per = warp_words(cap, cap2, MODE == MODE_LEARNED);
+    const uint32_t per = warp_words(cap, MODE == MODE_LEARNED);
     uint32_t *base = smem + warp * per;
     WarpMem wm;
     wm.fac = reinterpret_cast<uint64_t *>(base);
@@ -152,9 +150,8 @@ __device__ __forceinline__ WarpMem warp_mem(uint64_t *smem64, uint32_t cap, cons
     wm.tneq = base + 79;
     wm.S0 = base + kWarpHeaderWords;
     wm.S1 = wm.S0 + cap;
-    wm.S2 = wm.S1 + cap;
-    wm.htile = reinterpret_cast<uint16_t *>(wm.S2 + cap2);
-    wm.score = wm.S2 + cap2 + kHTileWords;
+    wm.htile = reinterpret_cast<uint16_t *>(wm.S1 + cap);
+    wm.score = wm.S1 + cap + kHTileWords;
     wm.W = W;
     wm.W2b = reinterpret_cast<const uint16_t *>(W + 4482);
     return wm;
@@ -457,25 +454,12 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 const bool drop = p.reuse[j] == 2;
                 const uint32_t P = prev_size;
                 const uint32_t off = (has_lo && lo >= vj1) ? prev_off : 0u;
-                // the kept elements exceed the bound, so only N(v_{j-1}) above it
-                // is tested: staged on chip when it fits the third buffer
-                int n2 = -1;
-                if (!kCompact && drop && a.cap2) {   // the compact variant runs edge-induced plans only
-                    const uint64_t ds = above(j - 1, b, en);
-                    // staging pays when the list is not much longer than the elements tested
-                    if (en - ds <= a.cap2 && en - ds <= 4ull * (P - off) + 64) {
-                        for (uint64_t q = ds + lane; q < en; q += 32) wm.S2[q - ds] = __ldg(g.col + q);
-                        n2 = (int)(en - ds);
-                        __syncwarp();
-                    }
-                }
                 for (uint32_t base = off; base < P; base += 32) {
                     const uint32_t idx = base + lane;
                     const bool valid = idx < P;
                     const uint32_t y = valid ? Sp[idx] : 0u;
                     bool ok = valid && (!has_lo || y > lo) && y != vj1;
-                    if (drop) ok = ok && !(n2 >= 0 ? lane_contains_shared(wm.S2, (uint32_t)n2, y)
-                                                   : lane_contains(g.col + b, en - b, y));
+                    if (drop) ok = ok && !lane_contains(g.col + b, en - b, y);
                     const unsigned m = __ballot_sync(kFull, ok);
                     if (ok) Sc[count + __popc(m & lanemask_lt())] = y;
                     count += __popc(m);
@@ -527,31 +511,10 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 // it, and its vertex when y could equal it (a non-edge not
                 // below the bound y already exceeds; membership in N(v_i)
                 // rules out y = v_i, the graph having no loops)
-                // (vertex-induced) the shortest non-neighbour list, above the
-                // bound, staged in the third buffer when it fits
-                int neg_staged = -1;
-                uint32_t n2 = 0;
-                if (!kCompact && a.cap2 && p.induced && !empty) {
-                    const bool nb = (int)lane < j && !((back >> lane) & 1u);
-                    const uint64_t nkey = nb ? (((le - lb) << 5) | lane) : ~0ull;
-                    const uint64_t best = warp_min_u64(nkey);
-                    if (best != ~0ull) {
-                        const int q = (int)(best & 31u);
-                        const uint64_t qb = __shfl_sync(kFull, lb, q), qe = __shfl_sync(kFull, le, q);
-                        const uint64_t qs = above(q, qb, qe);
-                        if (qe - qs <= a.cap2 && qe - qs <= 4ull * (de - dstart) + 64) {
-                            for (uint64_t t = qs + lane; t < qe; t += 32) wm.S2[t - qs] = __ldg(g.col + t);
-                            n2 = (uint32_t)(qe - qs);
-                            neg_staged = q;
-                            __syncwarp();
-                        }
-                    }
-                }
-                {
+                if constexpr (kCompact) {
                     const bool edge = (int)lane < j && ((back >> lane) & 1u);
                     const bool nonedge = (int)lane < j && !edge;
-                    const bool test = (edge && (int)lane != driver && (int)lane != staged) ||
-                                      (nonedge && p.induced && (int)lane != neg_staged);
+                    const bool test = (edge && (int)lane != driver && (int)lane != staged) || (nonedge && p.induced);
                     const bool neq = nonedge && !(has_lo && wm.v[lane] <= lo);
                     const unsigned tm = __ballot_sync(kFull, test), nm = __ballot_sync(kFull, neq);
                     if (test) {
@@ -564,14 +527,32 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                     nneq = __popc(nm);
                     __syncwarp();
                 }
+                // the unrolled variant (vertex-induced batches and single runs)
+                // keeps the per-position form: its four inlined copies overlap the
+                // global non-edge searches, which the table form measured slower on
                 auto pred = [&](uint32_t y) -> bool {
                     bool ok = true;
-                    for (int t = 0; t < nneq; t++) ok = ok && y != wm.tneq[t];
-                    if (staged >= 0) ok = ok && lane_contains_shared(Sp, plen, y);
-                    if (neg_staged >= 0) ok = ok && !lane_contains_shared(wm.S2, n2, y);
-                    for (int t = 0; t < ntest; t++) {
-                        const uint32_t ln = wm.tlen[t];
-                        ok = ok && (lane_contains(g.col + wm.tptr[t], ln & 0x7FFFFFFFu, y) != (ln >> 31));
+                    if constexpr (kCompact) {
+                        for (int t = 0; t < nneq; t++) ok = ok && y != wm.tneq[t];
+                        if (staged >= 0) ok = ok && lane_contains_shared(Sp, plen, y);
+                        for (int t = 0; t < ntest; t++) {
+                            const uint32_t ln = wm.tlen[t];
+                            ok = ok && (lane_contains(g.col + wm.tptr[t], ln & 0x7FFFFFFFu, y) != (ln >> 31));
+                        }
+                    } else {
+                        for (int i = 0; i < j; i++) {
+                            const uint64_t b = __shfl_sync(kFull, lb, i);
+                            const uint64_t en2 = __shfl_sync(kFull, le, i);
+                            ok = ok && (y != wm.v[i]);
+                            const bool edge = (back >> i) & 1u;
+                            if (edge) {
+                                if (i == driver) continue;
+                                if (i == staged) ok = ok && lane_contains_shared(Sp, plen, y);
+                                else ok = ok && lane_contains(g.col + b, en2 - b, y);
+                            } else if (p.induced) {
+                                ok = ok && !lane_contains(g.col + b, en2 - b, y);
+                            }
+                        }
                     }
                     return ok;
                 };
@@ -780,23 +761,10 @@ inline int kernel_mode(int mode, bool single) {
 // ------------------------------------------------------------------ launch shape
 struct Shape {
     uint32_t blocks, warps, cap, chunk;
-    uint32_t cap2;   // third buffer (vertex-induced plans), 0 = none
 };
 
-// Vertex-induced plans in the uniform modes get a third buffer of up to 512
-// entries for a staged non-neighbour list (3 x 512 entries per warp still
-// leave room for 4 resident blocks of 8 warps).
-#ifndef GPM_THIRD_MAX
-#define GPM_THIRD_MAX 512
-#endif
-inline uint32_t third_buffer(int kmode, bool induced, uint32_t cap) {
-    const uint32_t c = cap < GPM_THIRD_MAX ? cap : GPM_THIRD_MAX;
-    return (induced && (kmode == MODE_INTERSECT || kmode == MODE_INTERSECT_SINGLE)) ? ((c + 1u) & ~1u) : 0;
-}
-
-
 inline size_t smem_bytes(const Shape &sh, int mode) {
-    const size_t per = warp_words(sh.cap, sh.cap2, mode == MODE_LEARNED);
+    const size_t per = warp_words(sh.cap, mode == MODE_LEARNED);
     return (size_t)sh.warps * per * sizeof(uint32_t) +
            (mode == MODE_LEARNED ? kMlpSmemFloats * sizeof(float) : 0);
 }
@@ -840,7 +808,6 @@ inline Shape pick_shape(gpm_graph *h, const gpm_config *cfg, uint64_t count) {
     sh.cap = (cfg && cfg->cap) ? cfg->cap : 0;   // 0: fit_cap at launch
     sh.blocks = (cfg && cfg->grid_blocks) ? cfg->grid_blocks : 0;
     sh.chunk = kChunk;
-    sh.cap2 = 0;
     return sh;
 }
 
