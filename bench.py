@@ -47,8 +47,8 @@ WORKLOADS = {
                "workload": "R-MAT scale 22, edge factor 16 (a,b,c = 0.57,0.19,0.19), 4-clique + 5-clique NS "
                            "eager-verify"},
 }
-COMPANIONS = ["er-triangle", "rmat24-batch", "chunglu-needle", "selector", "complex", "gs-variants", "profiler",
-              "nsbase"]
+COMPANIONS = ["er-triangle", "rmat24-batch", "chunglu-needle", "chunglu-needle-capped", "selector", "complex",
+              "gs-variants", "profiler", "nsbase"]
 
 
 def parse():
@@ -471,6 +471,47 @@ def selector_study(api, G, eps=0.05, delta=0.01, time_cap=10.0):
 
 
 # ------------------------------------------------------------------ companion workloads
+def needle_row(api, g, og, name, colors, ns_seconds):
+    """Exact count (120 s budget), NS, GS per colour count, hybrid and learned NS on one
+    pattern; rel_err against the exact count (a lower bound when it did not finish)."""
+    row = {}
+    r, te = _timed(lambda: g.estimate(name, scheme=api.EXACT, max_seconds=120.0))
+    exact = r["exact_count"]
+    row["exact"] = {"count": exact, "seconds": te, "complete": bool(r["converged"])}
+
+    def err(x):
+        return abs(x - exact) / max(exact, 1)
+    r, t = _timed(lambda: g.estimate(name, eps=EPS, delta=DELTA, seed=1, window=WINDOW, n_max=1 << 36,
+                                     max_seconds=ns_seconds))
+    row["ns"] = {"seconds": t, "estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"],
+                 "converged": r["converged"], "rel_err": err(r["estimate"])}
+    for c in colors:
+        r, t = _timed(lambda: g.estimate(name, scheme=api.GS, seed=1, colors=c))
+        row["gs_c%d" % c] = {"seconds": t, "estimate": r["estimate"], "sparsified_count": r["exact_count"],
+                             "rel_err": err(r["estimate"]), "preproc_s": r["t_preproc_s"]}
+    r, t = _timed(lambda: g.estimate(name, scheme=api.HYBRID, eps=EPS, delta=DELTA, seed=1, window=WINDOW,
+                                     n_max=1 << 36, max_seconds=ns_seconds, colors=colors[-1]))
+    row["hybrid"] = {"seconds": t, "scheme": {0: "NS", 1: "GS"}.get(r["scheme_used"], r["scheme_used"]),
+                     "estimate": r["estimate"], "pilot_s": r["t_pilot_s"], "rel_err": err(r["estimate"])}
+    prop = api.Proposal(seed=1)
+    (loss, rows), ttrain = _timed(lambda: prop.train(g, name, seed=11, samples=1 << 21, epochs=3, batch=8192,
+                                                     lr=3e-3))
+    r, t = _timed(lambda: g.estimate(name, scheme=api.NS_LEARNED, eps=EPS, delta=DELTA, seed=1, window=WINDOW,
+                                     n_max=1 << 36, max_seconds=ns_seconds, mlp=prop))
+    row["learned"] = {"seconds": t, "train_s": ttrain, "train_rows": rows, "estimate": r["estimate"],
+                      "eps_hat": r["eps_hat"], "samples": r["samples"], "converged": r["converged"],
+                      "rel_err": err(r["estimate"])}
+    for variant, kw in (("plain", {}), ("learned", {"mlp": prop})):
+        sm = g.sample_sums(name, seed=9, first=0, count=1 << 22, **kw)
+        mu = sm.sum / sm.n
+        row[variant + "_cv2"] = (sm.sumsq / sm.n - mu * mu) / (mu * mu) if mu > 0 else None
+        row[variant + "_hit_rate"] = sm.hits / sm.n
+    if og is not None:
+        # the oracle's Algorithm 3 on every host core, capped at 120 s
+        row["cpu_oracle"] = oracle_online_parallel(og, name, EPS, DELTA, 1, WINDOW, 1 << 34, 120.0)
+    return row
+
+
 def companion(args):
     """One JSON line per companion workload (1 GPU)."""
     import torch
@@ -537,49 +578,21 @@ def companion(args):
                     "all_converged": all(r["converged"] for r in res),
                     "per_job": {nm: {"estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"]}
                                 for nm, r in zip(names, res)}})
-    elif args.config == "chunglu-needle":
-        # Chung-Lu, 8M vertices, exponent 2.1, mean degree 20, 200 planted 12-cliques
+    elif args.config in ("chunglu-needle", "chunglu-needle-capped"):
+        # Chung-Lu, 8M vertices, exponent 2.1, mean degree 20, 200 planted 12-cliques; weights
+        # capped at sqrt(sum w) (a dense hub core that holds almost every clique), or at 24 (no
+        # hub core: the planted cliques are the needles and the exact count finishes)
+        capped = args.config == "chunglu-needle-capped"
         rp, col = G.chung_lu(8_000_000, gamma=2.1, mean_degree=20.0, n_cliques=200, clique_size=12, seed=4,
-                             device="cuda")
+                             device="cuda", w_max=24.0 if capped else None)
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         g = api.Graph(rp, col)
         out.update({"n": g.n, "m": g.m, "max_degree": g.max_degree})
         og = None if args.no_cpu_baseline else oracle_graph(*G.to_numpy(rp, col))
         for name in ("7-clique", "8-clique"):
-            row = {}
-            r, te = _timed(lambda: g.estimate(name, scheme=api.EXACT, max_seconds=120.0))
-            exact = r["exact_count"]
-            row["exact"] = {"count": exact, "seconds": te, "complete": bool(r["converged"])}
-            r, t = _timed(lambda: g.estimate(name, eps=EPS, delta=DELTA, seed=1, window=WINDOW, n_max=1 << 32,
-                                             max_seconds=60.0))
-            row["ns"] = {"seconds": t, "estimate": r["estimate"], "eps_hat": r["eps_hat"], "samples": r["samples"],
-                         "converged": r["converged"], "rel_err": abs(r["estimate"] - exact) / max(exact, 1)}
-            r, t = _timed(lambda: g.estimate(name, scheme=api.GS, seed=1, colors=8))
-            row["gs_c8"] = {"seconds": t, "estimate": r["estimate"], "sparsified_count": r["exact_count"],
-                            "rel_err": abs(r["estimate"] - exact) / max(exact, 1), "preproc_s": r["t_preproc_s"]}
-            r, t = _timed(lambda: g.estimate(name, scheme=api.HYBRID, eps=EPS, delta=DELTA, seed=1, window=WINDOW,
-                                             n_max=1 << 32, max_seconds=60.0, colors=8))
-            row["hybrid"] = {"seconds": t, "scheme": {0: "NS", 1: "GS"}.get(r["scheme_used"], r["scheme_used"]),
-                             "estimate": r["estimate"], "pilot_s": r["t_pilot_s"],
-                             "rel_err": abs(r["estimate"] - exact) / max(exact, 1)}
-            prop = api.Proposal(seed=1)
-            (loss, rows), ttrain = _timed(lambda: prop.train(g, name, seed=11, samples=1 << 21, epochs=3,
-                                                             batch=8192, lr=3e-3))
-            r, t = _timed(lambda: g.estimate(name, scheme=api.NS_LEARNED, eps=EPS, delta=DELTA, seed=1,
-                                             window=WINDOW, n_max=1 << 32, max_seconds=60.0, mlp=prop))
-            row["learned"] = {"seconds": t, "train_s": ttrain, "train_rows": rows, "estimate": r["estimate"],
-                              "eps_hat": r["eps_hat"], "samples": r["samples"], "converged": r["converged"],
-                              "rel_err": abs(r["estimate"] - exact) / max(exact, 1)}
-            for variant, kw in (("plain", {}), ("learned", {"mlp": prop})):
-                sm = g.sample_sums(name, seed=9, first=0, count=1 << 22, **kw)
-                mu = sm.sum / sm.n
-                row[variant + "_cv2"] = (sm.sumsq / sm.n - mu * mu) / (mu * mu) if mu > 0 else None
-                row[variant + "_hit_rate"] = sm.hits / sm.n
-            if og is not None:
-                # the oracle's Algorithm 3 on every host core, capped at 120 s
-                row["cpu_oracle"] = oracle_online_parallel(og, name, EPS, DELTA, 1, WINDOW, 1 << 34, 120.0)
-            out[name] = row
+            out[name] = needle_row(api, g, og, name, colors=(2, 4, 8) if capped else (8,),
+                                   ns_seconds=30.0 if capped else 60.0)
     elif args.config == "selector":
         out.update(selector_study(api, G))
     elif args.config == "complex":

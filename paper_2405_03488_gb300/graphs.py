@@ -151,16 +151,16 @@ def rmat(scale, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=2, device="cpu", re
 
 
 def chung_lu(n, gamma=2.1, mean_degree=20.0, n_cliques=200, clique_size=12, seed=4,
-             device="cpu", relabel=True, offset=10.0):
+             device="cpu", relabel=True, offset=10.0, w_max=None):
     """Chung-Lu graph with expected degrees w_i ~ (i + offset)^(-1/(gamma-1)),
-    scaled to the mean degree and capped at sqrt(sum w); n * mean / 2 endpoint
-    pairs drawn from the weight distribution; plus planted cliques on uniformly
-    chosen vertex sets."""
+    scaled to the mean degree and capped at sqrt(sum w) (or at w_max when given);
+    n * mean / 2 endpoint pairs drawn from the weight distribution; plus planted
+    cliques on uniformly chosen vertex sets."""
     g = _gen(seed, device)
     i = torch.arange(n, dtype=torch.float64, device=device)
     w = (i + offset).pow(-1.0 / (gamma - 1.0))
     w = w * (n * mean_degree / w.sum())
-    w = torch.clamp(w, max=math.sqrt(float(w.sum())))
+    w = torch.clamp(w, max=math.sqrt(float(w.sum())) if w_max is None else float(w_max))
     cdf = torch.cumsum(w, 0)
     cdf = cdf / cdf[-1]
     m = int(n * mean_degree / 2)

@@ -78,6 +78,23 @@ def test_two_pass_and_odd_shapes_bit_exact(cap, warps, blocks):
         assert_same_records(gpu, cpu, k)
 
 
+@pytest.mark.parametrize("cap", [64, 96, 160])
+def test_sampled_list_searches_bit_exact(cap):
+    """Lists longer than the on-chip buffer are searched through an on-chip
+    sample of every step-th entry (the partner list of a step, N(v_{j-1}) when
+    S_j is cut from S_{j-1}, the non-neighbours removed from S_{j-1} in
+    vertex-induced plans): degrees of 100-200 against buffers of 64-160 entries
+    take every one of those paths, with uneven segment lengths."""
+    for rp, col in (G.erdos_renyi(300, 0.45, seed=8), G.rmat(11, 24, seed=6)):
+        g, og = pair(rp, col)
+        for name, induced in (("4-clique", False), ("5-clique", False), ("diamond", True), ("3-star", True),
+                              ("tailed-triangle", True), ("4-cycle", True), ("house", False)):
+            k, edges = G.pattern(name)
+            gpu = g.trace((k, edges, induced), seed=4, first=0, count=1200, cap=cap)
+            _, cpu = O.ns_run(og, O.plan(k, edges, induced), seed=4, first=0, count=1200, trace=True)
+            assert_same_records(gpu, cpu, k)
+
+
 def test_sums_match_oracle_er_triangle_1e6():
     """ER G(n=10^4, p=0.002), triangle, 10^6 samples, seed 1."""
     rp, col = G.erdos_renyi(10_000, 0.002, seed=1)
