@@ -208,7 +208,8 @@ typedef struct {
 /* Load a graph (Sec. 6: symmetric CSR without loops or duplicates).
  *  n        vertex count (< 2^32 - 1)
  *  row_ptr  n + 1 offsets into col, row_ptr[0] = 0 (uint64)
- *  col      row_ptr[n] neighbour ids, each list sorted ascending (uint32)
+ *  col      row_ptr[n] neighbour ids, each list sorted ascending (uint32);
+ *           every degree below 2^31 (else GPM_ERR_GRAPH)
  *  flags    GPM_DEVICE_PTRS: both arrays are device pointers the handle borrows
  *           (the caller keeps them alive and unchanged until gpm_free_graph);
  *           otherwise they are host arrays that the call copies.

@@ -94,17 +94,64 @@ __device__ __forceinline__ uint64_t lane_find(const uint32_t *__restrict__ a, ui
     return __ldg(b) == x ? (uint64_t)(b - a) : ~0ull;
 }
 
+// 32-bit forms of the three searches for one neighbour list (fewer than 2^31
+// entries: the load rejects larger degrees).  Same probes in the same order as
+// the forms above; positions are offsets from the list's first entry, so index
+// arithmetic stays in 32-bit registers.
+__device__ __forceinline__ uint32_t warp_upper_bound32(const uint32_t *__restrict__ a, uint32_t len,
+                                                       uint32_t key) {
+    const unsigned lane = lane_id();
+    uint32_t lo = 0, hi = len;
+    while (hi - lo > 32) {
+        const uint32_t step = ((hi - lo - 1u) >> 5) + 1u;   // ceil((hi - lo) / 32)
+        const uint32_t pos = lo + lane * step;
+        const bool le = (pos < hi) && (__ldg(a + pos) <= key);
+        const unsigned m = __ballot_sync(kFull, le);
+        const uint32_t c = (uint32_t)__popc(m);
+        if (c == 0) return lo;
+        const uint32_t nlo = lo + (c - 1u) * step + 1u;
+        const uint32_t nhi = lo + c * step;
+        lo = nlo;
+        hi = nhi < hi ? nhi : hi;
+    }
+    const uint32_t pos = lo + lane;
+    const bool le = (pos < hi) && (__ldg(a + pos) <= key);
+    return lo + (uint32_t)__popc(__ballot_sync(kFull, le));
+}
+
+__device__ __forceinline__ bool lane_contains32(const uint32_t *__restrict__ a, uint32_t len, uint32_t x) {
+    if (len == 0) return false;
+    uint32_t b = 0, n = len;
+    while (n > 1) {
+        const uint32_t half = n >> 1;
+        b = (__ldg(a + b + half) <= x) ? b + half : b;
+        n -= half;
+    }
+    return __ldg(a + b) == x;
+}
+
+// offset of x in a[0, len), or 0xFFFFFFFF when absent
+__device__ __forceinline__ uint32_t lane_find32(const uint32_t *__restrict__ a, uint32_t len, uint32_t x) {
+    if (len == 0) return 0xFFFFFFFFu;
+    uint32_t b = 0, n = len;
+    while (n > 1) {
+        const uint32_t half = n >> 1;
+        b = (__ldg(a + b + half) <= x) ? b + half : b;
+        n -= half;
+    }
+    return __ldg(a + b) == x ? b : 0xFFFFFFFFu;
+}
+
 // Same on a shared-memory list.
 __device__ __forceinline__ bool lane_contains_shared(const uint32_t *a, uint32_t len, uint32_t x) {
     if (len == 0) return false;
-    const uint32_t *b = a;
-    uint32_t n = len;
+    uint32_t b = 0, n = len;
     while (n > 1) {
         const uint32_t half = n >> 1;
-        b = (b[half] <= x) ? b + half : b;
+        b = (a[b + half] <= x) ? b + half : b;
         n -= half;
     }
-    return *b == x;
+    return a[b] == x;
 }
 
 }  // namespace gpm

@@ -403,6 +403,11 @@ extern "C" gpm_status gpm_load_csr(uint64_t n, const uint64_t *row_ptr, const ui
     g->d.uoff = g->uoff;
     g->d.m = m;
     g->max_degree = maxd_h;
+    if (maxd_h >= (1ull << 31)) {
+        // the sampler addresses entries inside one list with 32-bit offsets
+        set_error("gpm_load_csr: a vertex of degree 2^31 or more is not supported");
+        return fail(GPM_ERR_GRAPH);
+    }
     // optional first-edge table; without memory for it the sampler searches uoff
     g->d.edges = nullptr;
     if (m > 0 && pool_alloc((void **)&g->edges, sizeof(uint64_t) * m, st) == cudaSuccess) {

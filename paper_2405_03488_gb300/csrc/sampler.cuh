@@ -37,6 +37,23 @@ constexpr uint32_t kLearnedMax = 256;   // larger candidate sets are drawn unifo
 #ifndef GPM_REUSE_STREAM_BIAS
 #define GPM_REUSE_STREAM_BIAS 0
 #endif
+// a partner list longer than the on-chip buffer is staged window by window
+// (compact variant) instead of being searched in global memory
+#ifndef GPM_PARTNER_WINDOWS
+#define GPM_PARTNER_WINDOWS 1
+#endif
+// ... while the partner is at most this many times longer than the driver
+// (a much longer partner is cheaper to search per driver entry; 8, 16, 32 and
+// unbounded measured 1.55, 1.66, 1.72 and 1.65 times the global search on the
+// R-MAT 27 5-clique / 4-cycle batch)
+#ifndef GPM_WINDOW_RATIO
+#define GPM_WINDOW_RATIO 32
+#endif
+// staging copies: cp.async, all of a list's copies in flight at once and no
+// register round trip (1), or four loads per lane then stores (0)
+#ifndef GPM_STAGE_ASYNC
+#define GPM_STAGE_ASYNC 1
+#endif
 
 constexpr int kMlpFloats = 4481;        // 3->64->64->1 weights and biases
 constexpr int kW2Stride = 72;           // BF16 W2 rows and hidden tiles, padded against bank conflicts
@@ -168,6 +185,32 @@ __device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
 
+// Copies src[0, n) (global) to dst[0, n) (the warp's shared-memory buffer);
+// all lanes call it, and the caller's __syncwarp publishes the copy.
+__device__ __forceinline__ void stage_list(const uint32_t *__restrict__ src, uint32_t n, uint32_t *dst) {
+    const unsigned lane = lane_id();
+#if GPM_STAGE_ASYNC
+    const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(dst);
+    for (uint32_t idx = lane; idx < n; idx += 32)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d0 + 4u * idx), "l"(src + idx) : "memory");
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+#else
+    for (uint32_t base = 0; base < n; base += 128) {
+        uint32_t y[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t idx = base + 32 * u + lane;
+            y[u] = idx < n ? __ldg(src + idx) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t idx = base + 32 * u + lane;
+            if (idx < n) dst[idx] = y[u];
+        }
+    }
+#endif
+}
+
 }  // namespace gpm
 
 // The learned proposal's device code (features, MLP score, lookahead, draw).
@@ -220,7 +263,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
     if (M == 0) return out;
     const uint64_t e = index_map(word(0), M);
     uint32_t v0, v1;
-    uint64_t pos01 = ~0ull;  // index of v1 inside N(v0) in col, when known
+    uint64_t pos01a = ~0ull;  // index of v1 inside N(v0) in col, when known
     if (orient && g.edges) {
         const uint64_t pr = __ldg(g.edges + e);
         v0 = (uint32_t)pr;
@@ -228,28 +271,37 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
     } else if (orient) {
         const uint64_t u = warp_upper_bound(g.uoff, g.n + 1, e) - 1;
         v0 = (uint32_t)u;
-        pos01 = __ldg(g.up + u) + (e - __ldg(g.uoff + u));
-        v1 = __ldg(g.col + pos01);
+        pos01a = __ldg(g.up + u) + (e - __ldg(g.uoff + u));
+        v1 = __ldg(g.col + pos01a);
     } else {
         const uint64_t u = warp_upper_bound(g.row_ptr, g.n + 1, e) - 1;
         v0 = (uint32_t)u;
-        pos01 = e;
+        pos01a = e;
         v1 = __ldg(g.col + e);
     }
-    // lane i: CSR range [lb, le) of v_i and lu, the first entry above v_i
-    uint64_t lb = 0, le = 0, lu = 0;
+    // lane i: row start rb of v_i in col, its degree rn, and ru, the offset of
+    // its first neighbour above v_i (degrees are below 2^31, so offsets inside a
+    // list are 32-bit)
+    uint64_t rb = 0;
+    uint32_t rn = 0, ru = 0;
     if (lane == 0) {
-        lb = __ldg(g.row_ptr + v0);
-        le = __ldg(g.row_ptr + v0 + 1);
-        lu = __ldg(g.up + v0);
+        rb = __ldg(g.row_ptr + v0);
+        rn = (uint32_t)(__ldg(g.row_ptr + v0 + 1) - rb);
+        ru = (uint32_t)(__ldg(g.up + v0) - rb);
         wm.v[0] = v0;
         wm.v[1] = v1;
     } else if (lane == 1) {
-        lb = __ldg(g.row_ptr + v1);
-        le = __ldg(g.row_ptr + v1 + 1);
-        lu = __ldg(g.up + v1);
+        rb = __ldg(g.row_ptr + v1);
+        rn = (uint32_t)(__ldg(g.row_ptr + v1 + 1) - rb);
+        ru = (uint32_t)(__ldg(g.up + v1) - rb);
     }
+    // offset of v1 inside N(v0), when known
+    uint32_t pos01 = 0xFFFFFFFFu;
+    if (pos01a != ~0ull) pos01 = (uint32_t)(pos01a - __shfl_sync(kFull, rb, 0));
     __syncwarp();
+    // list of position i, as a pointer to its first entry and its length
+    auto row = [&](int i) -> const uint32_t * { return g.col + __shfl_sync(kFull, rb, i); };
+    auto deg = [&](int i) -> uint32_t { return __shfl_sync(kFull, rn, i); };
     out.depth = 2;
     double w = (double)M;
     uint64_t wu = M;
@@ -265,16 +317,17 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
         for (int i = 0; i < j; i++)
             if ((lm >> i) & 1u) lo = wm.v[i] > lo ? wm.v[i] : lo;
         const uint64_t r = word(j - 1);
-        // first index of position i's list [b, en) above the lower bound; the
-        // split at lu and the known slot of v1 in N(v0) shorten or skip the search
-        auto above = [&](int i, uint64_t b, uint64_t en) -> uint64_t {
-            const uint64_t ui = __shfl_sync(kFull, lu, i);
-            if (!has_lo) return b;
+        // offset of the first entry of position i's list L (n entries) above
+        // the lower bound; the split at ru and the known slot of v1 in N(v0)
+        // shorten or skip the search
+        auto above = [&](int i, const uint32_t *L, uint32_t n) -> uint32_t {
+            const uint32_t ui = __shfl_sync(kFull, ru, i);
+            if (!has_lo) return 0u;
             const uint32_t vi = wm.v[i];
             if (lo == vi) return ui;
-            if (i == 0 && lo == wm.v[1] && pos01 != ~0ull) return pos01 + 1;
-            if (lo > vi) return ui + warp_upper_bound(g.col + ui, en - ui, lo);
-            return b + warp_upper_bound(g.col + b, ui - b, lo);
+            if (i == 0 && lo == wm.v[1] && pos01 != 0xFFFFFFFFu) return pos01 + 1u;
+            if (lo > vi) return ui + warp_upper_bound32(L + ui, n - ui, lo);
+            return warp_upper_bound32(L, ui, lo);
         };
         uint64_t size = 0;
         uint32_t x = 0;
@@ -289,27 +342,27 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 bool ok = true;
                 for (int q = 0; q < i; q++) {
                     if (!((back >> q) & 1u)) continue;
-                    const uint64_t bq = __shfl_sync(kFull, lb, q);
-                    const uint64_t eq = __shfl_sync(kFull, le, q);
-                    ok = ok && !lane_contains(g.col + bq, eq - bq, y);
+                    const uint32_t *Lq = row(q);
+                    const uint32_t nq = deg(q);
+                    ok = ok && !lane_contains32(Lq, nq, y);
                 }
                 return ok;
             };
-            uint64_t my_kept = 0;   // lane i: entries back-neighbour i adds to U_j
+            uint32_t my_kept = 0;   // lane i: entries back-neighbour i adds to U_j
             for (int i = 0; i < j; i++) {
                 if (!((back >> i) & 1u)) continue;
-                const uint64_t b = __shfl_sync(kFull, lb, i);
-                const uint64_t en = __shfl_sync(kFull, le, i);
-                uint64_t c = 0;
+                const uint32_t *L = row(i);
+                const uint32_t n = deg(i);
+                uint32_t c = 0;
                 if ((back & ((1u << i) - 1u)) == 0) {
-                    c = en - b;
+                    c = n;
                 } else {
-                    for (uint64_t base = b; base < en; base += 32) {
-                        const uint64_t idx = base + lane;
-                        const bool valid = idx < en;
-                        const uint32_t y = valid ? __ldg(g.col + idx) : 0u;
+                    for (uint32_t base = 0; base < n; base += 32) {
+                        const uint32_t idx = base + lane;
+                        const bool valid = idx < n;
+                        const uint32_t y = valid ? __ldg(L + idx) : 0u;
                         const bool ok = fresh(y, i) && valid;
-                        c += __popc(__ballot_sync(kFull, ok));
+                        c += (uint32_t)__popc(__ballot_sync(kFull, ok));
                     }
                 }
                 if ((int)lane == i) my_kept = c;
@@ -328,16 +381,16 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                     t -= c;
                     continue;
                 }
-                const uint64_t b = __shfl_sync(kFull, lb, i);
-                const uint64_t en = __shfl_sync(kFull, le, i);
+                const uint32_t *L = row(i);
+                const uint32_t n = deg(i);
                 if ((back & ((1u << i) - 1u)) == 0) {
-                    x = __ldg(g.col + b + t);
+                    x = __ldg(L + t);
                 } else {
                     uint64_t seen = 0;
-                    for (uint64_t base = b; base < en; base += 32) {
-                        const uint64_t idx = base + lane;
-                        const bool valid = idx < en;
-                        const uint32_t y = valid ? __ldg(g.col + idx) : 0u;
+                    for (uint32_t base = 0; base < n; base += 32) {
+                        const uint32_t idx = base + lane;
+                        const bool valid = idx < n;
+                        const uint32_t y = valid ? __ldg(L + idx) : 0u;
                         const bool ok = fresh(y, i) && valid;
                         const unsigned m = __ballot_sync(kFull, ok);
                         const uint64_t cm = __popc(m);
@@ -354,24 +407,24 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
             }
         } else if (MODE == MODE_CHECK) {
             const int pb = (int)p.last_back[j];
-            const uint64_t b = __shfl_sync(kFull, lb, pb);
-            const uint64_t en = __shfl_sync(kFull, le, pb);
-            const uint64_t start = above(pb, b, en);
-            size = en - start;
+            const uint32_t *L = row(pb);
+            const uint32_t n = deg(pb);
+            const uint32_t start = above(pb, L, n);
+            size = n - start;
             if (lane == 0) wm.fac[j] = size;
             if (size == 0) {
                 out.depth = j;
                 return out;
             }
-            x = __ldg(g.col + start + index_map(r, size));
+            x = __ldg(L + start + (uint32_t)index_map(r, size));
             bool okl = true;
             if ((int)lane < j) {
                 okl = (x != wm.v[lane]);
                 const bool edge = (p.back[j] >> lane) & 1u;
                 if (edge) {
-                    if ((int)lane != pb) okl = okl && lane_contains(g.col + lb, le - lb, x);
+                    if ((int)lane != pb) okl = okl && lane_contains32(g.col + rb, rn, x);
                 } else if (p.induced) {
-                    okl = okl && !lane_contains(g.col + lb, le - lb, x);
+                    okl = okl && !lane_contains32(g.col + rb, rn, x);
                 }
             }
             if (!__all_sync(kFull, okl)) {
@@ -381,7 +434,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
         } else {
             uint32_t *Sc = (j & 1) ? wm.S1 : wm.S0;
             uint32_t *Sp = (j & 1) ? wm.S0 : wm.S1;
-            uint64_t count = 0;
+            uint32_t count = 0;
             bool mat = true;
             const uint32_t back = p.back[j];
             if ((MODE == MODE_INTERSECT_SINGLE || (MODE == MODE_LEARNED && j == k - 1)) && !p.induced &&
@@ -390,45 +443,47 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 // bound without the matched vertices it holds, so |S_j| and its
                 // t-th element follow from their positions in the list alone
                 const int d = __ffs(back) - 1;
-                const uint64_t db = __shfl_sync(kFull, lb, d);
-                const uint64_t de = __shfl_sync(kFull, le, d);
-                const uint64_t dstart = above(d, db, de);
-                const uint64_t L = de - dstart;
-                const uint64_t q = ((int)lane < j && (int)lane != d) ? lane_find(g.col + dstart, L, wm.v[lane]) : ~0ull;
-                count = L - (uint64_t)__popc(__ballot_sync(kFull, q != ~0ull));
+                const uint32_t *DL = row(d);
+                const uint32_t dn = deg(d);
+                const uint32_t ds = above(d, DL, dn);
+                const uint32_t *S = DL + ds;
+                const uint32_t L = dn - ds;
+                const uint32_t q = ((int)lane < j && (int)lane != d) ? lane_find32(S, L, wm.v[lane]) : 0xFFFFFFFFu;
+                count = L - (uint32_t)__popc(__ballot_sync(kFull, q != 0xFFFFFFFFu));
                 if (count) {
                     // smallest list index with t kept entries before it
-                    const uint64_t t = index_map(r, count);
-                    uint64_t idx = t;
+                    const uint32_t t = (uint32_t)index_map(r, count);
+                    uint32_t idx = t;
                     for (;;) {
-                        const uint64_t nx = t + (uint64_t)__popc(__ballot_sync(kFull, q <= idx));
+                        const uint32_t nx = t + (uint32_t)__popc(__ballot_sync(kFull, q <= idx));
                         if (nx == idx) break;
                         idx = nx;
                     }
-                    x = __ldg(g.col + dstart + idx);
+                    x = __ldg(S + idx);
                 }
                 mat = false;
             } else if (p.reuse[j] == 1 && prev_mat) {
                 // S_j = S_{j-1} (on chip) cut by N(v_{j-1}) above the bound;
                 // when the bound is at least v_{j-1}, only the part of S_{j-1}
                 // after v_{j-1} can qualify
-                const uint64_t b = __shfl_sync(kFull, lb, j - 1);
-                const uint64_t en = __shfl_sync(kFull, le, j - 1);
-                const uint64_t start = above(j - 1, b, en);
-                const uint64_t L = en - start;
+                const uint32_t *NL = row(j - 1);
+                const uint32_t nn = deg(j - 1);
+                const uint32_t start = above(j - 1, NL, nn);
+                const uint32_t *A = NL + start;
+                const uint32_t L = nn - start;
                 const uint32_t off = (has_lo && lo >= wm.v[j - 1]) ? prev_off : 0u;
                 const uint32_t P = prev_size;
-                if (L <= (uint64_t)GPM_REUSE_STREAM_FACTOR * (P - off) + GPM_REUSE_STREAM_BIAS) {
-                    for (uint64_t base = start; base < en; base += 128) {
+                if (L <= (uint32_t)GPM_REUSE_STREAM_FACTOR * (P - off) + GPM_REUSE_STREAM_BIAS) {
+                    for (uint32_t base = 0; base < L; base += 128) {
                         uint32_t y[4];
 #pragma unroll
                         for (int u = 0; u < 4; u++) {
-                            const uint64_t idx = base + 32 * u + lane;
-                            y[u] = idx < en ? __ldg(g.col + idx) : 0u;
+                            const uint32_t idx = base + 32 * u + lane;
+                            y[u] = idx < L ? __ldg(A + idx) : 0u;
                         }
 #pragma unroll
                         for (int u = 0; u < 4; u++) {
-                            const bool ok = (base + 32 * u + lane < en) && lane_contains_shared(Sp + off, P - off, y[u]);
+                            const bool ok = (base + 32 * u + lane < L) && lane_contains_shared(Sp + off, P - off, y[u]);
                             const unsigned m = __ballot_sync(kFull, ok);
                             if (ok) Sc[count + __popc(m & lanemask_lt())] = y[u];
                             count += __popc(m);
@@ -439,7 +494,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                         const uint32_t idx = base + lane;
                         const bool valid = idx < P;
                         const uint32_t y = valid ? Sp[idx] : 0u;
-                        const bool ok = valid && (!has_lo || y > lo) && lane_contains(g.col + start, L, y);
+                        const bool ok = valid && (!has_lo || y > lo) && lane_contains32(A, L, y);
                         const unsigned m = __ballot_sync(kFull, ok);
                         if (ok) Sc[count + __popc(m & lanemask_lt())] = y;
                         count += __popc(m);
@@ -448,8 +503,8 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
             } else if (p.reuse[j] >= 2 && prev_mat) {
                 // S_j = S_{j-1} (on chip) above the bound, without v_{j-1}, and
                 // (vertex-induced) without N(v_{j-1})
-                const uint64_t b = __shfl_sync(kFull, lb, j - 1);
-                const uint64_t en = __shfl_sync(kFull, le, j - 1);
+                const uint32_t *NL = row(j - 1);
+                const uint32_t nn = deg(j - 1);
                 const uint32_t vj1 = wm.v[j - 1];
                 const bool drop = p.reuse[j] == 2;
                 const uint32_t P = prev_size;
@@ -459,7 +514,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                     const bool valid = idx < P;
                     const uint32_t y = valid ? Sp[idx] : 0u;
                     bool ok = valid && (!has_lo || y > lo) && y != vj1;
-                    if (drop) ok = ok && !lane_contains(g.col + b, en - b, y);
+                    if (drop) ok = ok && !lane_contains32(NL, nn, y);
                     const unsigned m = __ballot_sync(kFull, ok);
                     if (ok) Sc[count + __popc(m & lanemask_lt())] = y;
                     count += __popc(m);
@@ -468,39 +523,45 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 // driver: shortest back-neighbour list, streamed; partner: the
                 // next shortest, staged on chip when its part above the bound fits
                 const bool isback = (int)lane < j && ((back >> lane) & 1u);
-                const uint64_t key = isback ? (((le - lb) << 5) | lane) : ~0ull;
-                const int driver = (int)(warp_min_u64(key) & 31u);
-                const uint64_t key2 = warp_min_u64((int)lane == driver ? ~0ull : key);
-                const int partner = (key2 == ~0ull) ? -1 : (int)(key2 & 31u);
-                const uint64_t db = __shfl_sync(kFull, lb, driver);
-                const uint64_t de = __shfl_sync(kFull, le, driver);
-                const uint64_t dstart = above(driver, db, de);
-                bool empty = dstart >= de;
+                // shortest list first, lowest position on ties
+                const uint32_t mylen = isback ? rn : 0xFFFFFFFFu;
+                const uint32_t m1 = __reduce_min_sync(kFull, mylen);
+                const int driver = __ffs(__ballot_sync(kFull, isback && rn == m1)) - 1;
+                const bool other = isback && (int)lane != driver;
+                const uint32_t m2 = __reduce_min_sync(kFull, other ? rn : 0xFFFFFFFFu);
+                const unsigned pm = __ballot_sync(kFull, other && rn == m2);
+                const int partner = pm ? __ffs(pm) - 1 : -1;
+                const uint32_t *DL = row(driver);
+                const uint32_t dn = deg(driver);
+                const uint32_t dstart = above(driver, DL, dn);
+                const uint32_t *D = DL + dstart;
+                const uint32_t dlen = dn - dstart;
+                bool empty = dlen == 0;
                 int staged = -1;
                 uint32_t plen = 0;
+                // the partner's part above the bound; longer than the buffer, the
+                // compact variant stages it window by window (each window settles
+                // the driver entries up to its last element)
+                const uint32_t *Q = nullptr;
+                uint32_t qn = 0;
+                bool windowed = false;
                 if (partner >= 0 && !empty) {
-                    const uint64_t pb0 = __shfl_sync(kFull, lb, partner);
-                    const uint64_t pe = __shfl_sync(kFull, le, partner);
-                    const uint64_t ps = above(partner, pb0, pe);
-                    if (ps >= pe) {
+                    const uint32_t *PL = row(partner);
+                    const uint32_t pn = deg(partner);
+                    const uint32_t ps = above(partner, PL, pn);
+                    Q = PL + ps;
+                    qn = pn - ps;
+                    if (ps >= pn) {
                         empty = true;
-                    } else if (pe - ps <= a.cap) {
-                        for (uint64_t base = ps; base < pe; base += 128) {
-                            uint32_t y[4];
-#pragma unroll
-                            for (int u = 0; u < 4; u++) {
-                                const uint64_t idx = base + 32 * u + lane;
-                                y[u] = idx < pe ? __ldg(g.col + idx) : 0u;
-                            }
-#pragma unroll
-                            for (int u = 0; u < 4; u++) {
-                                const uint64_t idx = base + 32 * u + lane;
-                                if (idx < pe) Sp[idx - ps] = y[u];
-                            }
-                        }
+                    } else if (qn <= a.cap) {
+                        stage_list(Q, qn, Sp);
                         staged = partner;
-                        plen = (uint32_t)(pe - ps);
+                        plen = qn;
                         __syncwarp();
+                    } else if (kCompact && GPM_PARTNER_WINDOWS &&
+                               (uint64_t)qn <= (uint64_t)GPM_WINDOW_RATIO * dlen) {
+                        staged = partner;
+                        windowed = true;
                     }
                 }
                 int ntest = 0, nneq = 0;
@@ -519,8 +580,8 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                     const unsigned tm = __ballot_sync(kFull, test), nm = __ballot_sync(kFull, neq);
                     if (test) {
                         const int t = __popc(tm & lanemask_lt());
-                        wm.tptr[t] = lb;
-                        wm.tlen[t] = (uint32_t)(le - lb) | (nonedge ? 0x80000000u : 0u);
+                        wm.tptr[t] = rb;
+                        wm.tlen[t] = rn | (nonedge ? 0x80000000u : 0u);
                     }
                     if (neq) wm.tneq[__popc(nm & lanemask_lt())] = wm.v[lane];
                     ntest = __popc(tm);
@@ -530,89 +591,132 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 // the unrolled variant (vertex-induced batches and single runs)
                 // keeps the per-position form: its four inlined copies overlap the
                 // global non-edge searches, which the table form measured slower on
+                bool gpart = false;   // search the windowed partner in global memory
                 auto pred = [&](uint32_t y) -> bool {
                     bool ok = true;
                     if constexpr (kCompact) {
                         for (int t = 0; t < nneq; t++) ok = ok && y != wm.tneq[t];
-                        if (staged >= 0) ok = ok && lane_contains_shared(Sp, plen, y);
+                        if (staged >= 0)
+                            ok = ok && (gpart ? lane_contains32(Q, qn, y) : lane_contains_shared(Sp, plen, y));
                         for (int t = 0; t < ntest; t++) {
                             const uint32_t ln = wm.tlen[t];
-                            ok = ok && (lane_contains(g.col + wm.tptr[t], ln & 0x7FFFFFFFu, y) != (ln >> 31));
+                            ok = ok && (lane_contains32(g.col + wm.tptr[t], ln & 0x7FFFFFFFu, y) != (ln >> 31));
                         }
                     } else {
                         for (int i = 0; i < j; i++) {
-                            const uint64_t b = __shfl_sync(kFull, lb, i);
-                            const uint64_t en2 = __shfl_sync(kFull, le, i);
+                            const uint32_t *Li = row(i);
+                            const uint32_t ni = deg(i);
                             ok = ok && (y != wm.v[i]);
                             const bool edge = (back >> i) & 1u;
                             if (edge) {
                                 if (i == driver) continue;
                                 if (i == staged) ok = ok && lane_contains_shared(Sp, plen, y);
-                                else ok = ok && lane_contains(g.col + b, en2 - b, y);
+                                else ok = ok && lane_contains32(Li, ni, y);
                             } else if (p.induced) {
-                                ok = ok && !lane_contains(g.col + b, en2 - b, y);
+                                ok = ok && !lane_contains32(Li, ni, y);
                             }
                         }
                     }
                     return ok;
                 };
                 if (!empty) {
-                    for (uint64_t base = dstart; base < de; base += 128) {
+                    if constexpr (kCompact) {
+                    // one copy of pred (the element picked by selects); the
+                    // driver entries are settled window by window, a partner
+                    // staged whole (or none) being a single last window
+                    uint32_t pw = 0, dcur = 0;
+                    for (;;) {
+                        bool tail = true;
+                        uint32_t wlast = 0u;
+                        if (windowed) {
+                            const uint32_t wn = (qn - pw < a.cap) ? qn - pw : a.cap;
+                            __syncwarp();
+                            stage_list(Q + pw, wn, Sp);
+                            __syncwarp();
+                            plen = wn;
+                            pw += wn;
+                            tail = pw >= qn;
+                            wlast = Sp[wn - 1];
+                        }
+                        bool stop = false;
+                        for (uint32_t base = dcur; base < dlen && !stop; base += 128) {
+                            uint32_t y[4];
+#pragma unroll
+                            for (int u = 0; u < 4; u++) {
+                                const uint32_t idx = base + 32 * u + lane;
+                                y[u] = idx < dlen ? __ldg(D + idx) : 0u;
+                            }
+#pragma unroll 1
+                            for (int u = 0; u < 4; u++) {
+                                const uint32_t b = base + 32 * u;
+                                if (b >= dlen) break;
+                                const uint32_t yu = u == 0 ? y[0] : u == 1 ? y[1] : u == 2 ? y[2] : y[3];
+                                const bool in = (b + lane < dlen) && (tail || yu <= wlast);
+                                const bool ok = in && pred(yu);
+                                const unsigned m = __ballot_sync(kFull, ok);
+                                if (ok) {
+                                    const uint32_t pos = count + __popc(m & lanemask_lt());
+                                    if (pos < a.cap) Sc[pos] = yu;
+                                }
+                                count += __popc(m);
+                                if (!tail) {
+                                    // the entries up to the window's last element form a prefix
+                                    const unsigned im = __ballot_sync(kFull, in);
+                                    if (im != kFull) {
+                                        dcur = b + __popc(im);
+                                        stop = true;
+                                        break;
+                                    }
+                                }
+                            }
+                        }
+                        if (tail || !stop) break;
+                    }
+                    gpart = windowed;
+                    } else {
+                    for (uint32_t base = 0; base < dlen; base += 128) {
                         uint32_t y[4];
 #pragma unroll
                         for (int u = 0; u < 4; u++) {
-                            const uint64_t idx = base + 32 * u + lane;
-                            y[u] = idx < de ? __ldg(g.col + idx) : 0u;
+                            const uint32_t idx = base + 32 * u + lane;
+                            y[u] = idx < dlen ? __ldg(D + idx) : 0u;
                         }
-                        if constexpr (kCompact) {
-                        // one copy of pred: the element is picked by selects
-#pragma unroll 1
-                        for (int u = 0; u < 4; u++) {
-                            if (base + 32 * u >= de) break;
-                            const uint32_t yu = u == 0 ? y[0] : u == 1 ? y[1] : u == 2 ? y[2] : y[3];
-                            const bool ok = pred(yu) && (base + 32 * u + lane < de);
-                            const unsigned m = __ballot_sync(kFull, ok);
-                            if (ok) {
-                                const uint64_t pos = count + __popc(m & lanemask_lt());
-                                if (pos < a.cap) Sc[pos] = yu;
-                            }
-                            count += __popc(m);
-                        }
-                        } else {
 #pragma unroll
                         for (int u = 0; u < 4; u++) {
-                            if (base + 32 * u >= de) break;
-                            const bool ok = pred(y[u]) && (base + 32 * u + lane < de);
+                            if (base + 32 * u >= dlen) break;
+                            const bool ok = pred(y[u]) && (base + 32 * u + lane < dlen);
                             const unsigned m = __ballot_sync(kFull, ok);
                             if (ok) {
-                                const uint64_t pos = count + __popc(m & lanemask_lt());
+                                const uint32_t pos = count + __popc(m & lanemask_lt());
                                 if (pos < a.cap) Sc[pos] = y[u];
                             }
                             count += __popc(m);
                         }
-                        }
                     }
+                    }
+                }
+                if (!empty) {
                     mat = count <= a.cap;
                     if (!mat) {
                         if constexpr (kCompact) {
                         // second pass: locate the drawn element without storing the set
-                            const uint64_t target = index_map(r, count);
-                            uint64_t seen = 0;
+                            const uint32_t target = (uint32_t)index_map(r, count);
+                            uint32_t seen = 0;
                             bool found = false;
-                            for (uint64_t base = dstart; base < de && !found; base += 128) {
+                            for (uint32_t base = 0; base < dlen && !found; base += 128) {
                                 uint32_t y[4];
     #pragma unroll
                                 for (int u = 0; u < 4; u++) {
-                                    const uint64_t idx = base + 32 * u + lane;
-                                    y[u] = idx < de ? __ldg(g.col + idx) : 0u;
+                                    const uint32_t idx = base + 32 * u + lane;
+                                    y[u] = idx < dlen ? __ldg(D + idx) : 0u;
                                 }
     #pragma unroll 1
                                 for (int u = 0; u < 4; u++) {
-                                    if (found || base + 32 * u >= de) break;
+                                    if (found || base + 32 * u >= dlen) break;
                                     const uint32_t yu = u == 0 ? y[0] : u == 1 ? y[1] : u == 2 ? y[2] : y[3];
-                                    const bool ok = pred(yu) && (base + 32 * u + lane < de);
+                                    const bool ok = pred(yu) && (base + 32 * u + lane < dlen);
                                     const unsigned m = __ballot_sync(kFull, ok);
-                                    const uint64_t c = __popc(m);
+                                    const uint32_t c = __popc(m);
                                     if (seen + c > target) {
                                         const uint32_t rank = (uint32_t)(target - seen);
                                         const bool mine = ok && (uint32_t)__popc(m & lanemask_lt()) == rank;
@@ -625,23 +729,23 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                             }
                         } else {
                         // second pass: locate the drawn element without storing the set
-                            const uint64_t target = index_map(r, count);
-                            uint64_t seen = 0;
+                            const uint32_t target = (uint32_t)index_map(r, count);
+                            uint32_t seen = 0;
                             bool found = false;
-                            for (uint64_t base = dstart; base < de && !found; base += 128) {
+                            for (uint32_t base = 0; base < dlen && !found; base += 128) {
                                 uint32_t y[4];
     #pragma unroll
                                 for (int u = 0; u < 4; u++) {
-                                    const uint64_t idx = base + 32 * u + lane;
-                                    y[u] = idx < de ? __ldg(g.col + idx) : 0u;
+                                    const uint32_t idx = base + 32 * u + lane;
+                                    y[u] = idx < dlen ? __ldg(D + idx) : 0u;
                                 }
     #pragma unroll
                                 for (int u = 0; u < 4; u++) {
-                                    if (found || base + 32 * u >= de) break;
+                                    if (found || base + 32 * u >= dlen) break;
                                     const uint32_t yu = y[u];
-                                    const bool ok = pred(yu) && (base + 32 * u + lane < de);
+                                    const bool ok = pred(yu) && (base + 32 * u + lane < dlen);
                                     const unsigned m = __ballot_sync(kFull, ok);
-                                    const uint64_t c = __popc(m);
+                                    const uint32_t c = __popc(m);
                                     if (seen + c > target) {
                                         const uint32_t rank = (uint32_t)(target - seen);
                                         const bool mine = ok && (uint32_t)__popc(m & lanemask_lt()) == rank;
@@ -666,7 +770,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
             if (MODE == MODE_LEARNED && j <= k - 2 && mat && size <= kLearnedMax) {
                 uint64_t A = 0;
                 uint32_t ax = 0;
-                x = learned_pick(g, p, wm, Sc, (uint32_t)size, j, r, lb, le, a.mlp_tc != 0, &A, &ax);
+                x = learned_pick(g, p, wm, Sc, (uint32_t)size, j, r, rb, rb + rn, a.mlp_tc != 0, &A, &ax);
                 if (lane == 0) {
                     wm.fac[j] = A;
                     wm.aux[j] = ax;
@@ -684,9 +788,9 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
         }
         if (lane == 0) wm.v[j] = x;
         if ((int)lane == j && j + 1 < k) {
-            lb = __ldg(g.row_ptr + x);
-            le = __ldg(g.row_ptr + x + 1);
-            lu = __ldg(g.up + x);
+            rb = __ldg(g.row_ptr + x);
+            rn = (uint32_t)(__ldg(g.row_ptr + x + 1) - rb);
+            ru = (uint32_t)(__ldg(g.up + x) - rb);
         }
         __syncwarp();
         if (learned_step) {
@@ -713,14 +817,14 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
             int jj = 1;
             while ((jj + 1) * jj / 2 <= qq) jj++;
             const int ii = qq - jj * (jj - 1) / 2;
-            const uint64_t bi = __shfl_sync(kFull, lb, ii);
-            const uint64_t ei = __shfl_sync(kFull, le, ii);
+            const uint32_t *Li = row(ii);
+            const uint32_t ni = deg(ii);
             if (q < npairs) {
                 const uint32_t vi = wm.v[ii], vj = wm.v[jj];
                 bool good = vi != vj;
                 const bool edge = (p.back[jj] >> ii) & 1u;
                 if (good && (edge || p.induced)) {
-                    const bool adj = lane_contains(g.col + bi, ei - bi, vj);
+                    const bool adj = lane_contains32(Li, ni, vj);
                     good = edge ? adj : !adj;
                 }
                 if ((p.lower[jj] >> ii) & 1u) good = good && vi < vj;

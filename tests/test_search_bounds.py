@@ -1,10 +1,13 @@
-"""The index arithmetic of the sampler's search primitives (csrc/device.cuh),
-transcribed step for step and run on the CPU: every read stays inside the
-searched list and the answer is right, for every list length up to 300 and
-every key below, between and above the elements.  A per-lane halving search
-keeps b + n <= len (its first read b + n/2 < b + n, its last b < len); the
-warp's 32-ary upper bound reads a slot only below its open upper end, which
-never grows.  CPU only."""
+"""The index arithmetic of the sampler's search primitives (csrc/device.cuh)
+and of its windowed partner staging (csrc/sampler.cuh), transcribed step for
+step and run on the CPU: every read stays inside the searched list and the
+answer is right, for every list length up to 300 and every key below, between
+and above the elements.  A per-lane halving search keeps b + n <= len (its
+first read b + n/2 < b + n, its last b < len); the warp's 32-ary upper bound
+reads a slot only below its open upper end, which never grows (the 32-bit form
+computes the piece length as ((hi - lo - 1) >> 5) + 1, the same ceiling).
+The windowed staging settles every driver entry exactly once, in order, and
+reads the partner only inside its list.  CPU only."""
 import numpy as np
 import pytest
 
@@ -37,10 +40,10 @@ def lane_find(a, x, reads):
     return b if a[b] == x else None
 
 
-def warp_upper_bound(a, key, reads):
+def warp_upper_bound(a, key, reads, form32=False):
     lo, hi = 0, len(a)
     while hi - lo > 32:
-        step = (hi - lo + 31) // 32
+        step = (((hi - lo - 1) >> 5) + 1) if form32 else (hi - lo + 31) // 32
         le = []
         for lane in range(32):
             pos = lo + lane * step
@@ -81,6 +84,75 @@ def test_searches_stay_inside_the_list(seed):
             f = lane_find(a, x, reads)
             assert f == (a.index(x) if x in a else None)
             assert all(0 <= r < n for r in reads)
-            reads = []
-            assert warp_upper_bound(a, x, reads) == int(np.searchsorted(a, x, side="right"))
-            assert all(0 <= r < n for r in reads)
+            for form32 in (False, True):
+                reads = []
+                assert warp_upper_bound(a, x, reads, form32) == int(np.searchsorted(a, x, side="right"))
+                assert all(0 <= r < n for r in reads)
+
+
+def windowed_intersection(D, Q, cap, reads_q, reads_d):
+    """The compact sampler's step-2 loop with the partner Q (longer than the
+    buffer) staged in windows of cap entries: each window settles the driver
+    entries up to its last element (all of them in the last window), in
+    groups of 32 lanes read 128 at a time."""
+    dlen, qn = len(D), len(Q)
+    out = []
+    pw, dcur = 0, 0
+    while True:
+        wn = min(qn - pw, cap)
+        assert wn >= 1
+        win = []
+        for idx in range(wn):
+            reads_q.append(pw + idx)
+            win.append(Q[pw + idx])
+        pw += wn
+        tail = pw >= qn
+        wlast = win[-1]
+        stop = False
+        base = dcur
+        while base < dlen and not stop:
+            for u in range(4):
+                b = base + 32 * u
+                if b >= dlen:
+                    break
+                ins = []
+                for lane in range(32):
+                    idx = b + lane
+                    y = None
+                    if idx < dlen:
+                        reads_d.append(idx)
+                        y = D[idx]
+                    inside = idx < dlen and (tail or y <= wlast)
+                    ins.append(inside)
+                    if inside and y in win:
+                        out.append(y)
+                if not tail:
+                    c = sum(ins)
+                    assert ins == [True] * c + [False] * (32 - c)   # a prefix
+                    if c < 32:
+                        dcur = b + c
+                        stop = True
+                        break
+            base += 128
+        if tail or not stop:
+            break
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_windowed_partner_staging_settles_every_driver_entry_once(seed):
+    rng = np.random.default_rng(seed)
+    for trial in range(60):
+        universe = int(rng.integers(50, 5000))
+        dlen = int(rng.integers(1, min(universe, 400)))
+        qn = int(rng.integers(1, min(universe, 1500)))
+        D = np.sort(rng.choice(universe, size=dlen, replace=False)).tolist()
+        Q = np.sort(rng.choice(universe, size=qn, replace=False)).tolist()
+        for cap in (1, 7, 32, 64, 100, 832):
+            if qn <= cap:
+                continue
+            rq, rd = [], []
+            got = windowed_intersection(D, Q, cap, rq, rd)
+            assert got == sorted(set(D) & set(Q))
+            assert all(0 <= r < qn for r in rq) and all(0 <= r < dlen for r in rd)
+            assert len(set(rq)) == len(rq)     # every partner entry staged at most once
