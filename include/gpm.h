@@ -451,8 +451,10 @@ gpm_status gpm_mlp_loss_grad(gpm_graph *g, const float *w32, const float *feat, 
 
 /* Training rows from plain-NS records (DEVICE, n): for every step
  * 2 <= j <= k-2 a sample passed, the features of its chosen vertex vert[j]
- * (the lookahead is factor[j+1]) and label = hit; rows in record then step
- * order into DEVICE feat [n (k-3)][3] and label; *rows = rows written. */
+ * (the lookahead is factor[j+1]) and the progress label
+ * (d - j - 1) / (k - j - 1) in FP32, d = depth (k on a hit): 1 on a hit, 0
+ * when step j+1 found no candidate; rows in record then step order into
+ * DEVICE feat [n (k-3)][3] and label; *rows = rows written. */
 gpm_status gpm_proposal_features(gpm_graph *g, const gpm_pattern *pattern, const gpm_sample_record *recs,
                                  uint64_t n, float *feat, float *label, uint64_t *rows);
 

@@ -9,7 +9,9 @@
 // Training rows come from the plain sampler's records: at every step j <= k-2
 // a sample passed, the chosen vertex vert[j] with its degree, j and the size
 // of the next candidate set factor[j+1] (exactly the lookahead feature), and
-// the label 1 if the sample hit.  The loss is binary cross-entropy on the
+// the progress label (d - j - 1) / (k - j - 1), d the depth the sample reached
+// (k on a hit): 1 on a hit, 0 when the next step found no candidate, so rare
+// hits still leave a dense signal.  The loss is binary cross-entropy on the
 // logit z, averaged over rows; the trainer keeps FP32 master weights, updates
 // them with Adam, and exports BF16 copies (round to nearest even) for the
 // sampler.  Forward and backward run on 64-row tiles: per tile the block forms
@@ -94,7 +96,10 @@ __global__ void feature_write(const DGraph g, const gpm_sample_record *__restric
         feat[3 * o] = flog2p1(d);
         feat[3 * o + 1] = __int2float_rn(j);
         feat[3 * o + 2] = flog2p1(r.factor[j + 1]);
-        label[o] = r.hit ? 1.f : 0.f;
+        // progress label: the share of the remaining steps j+1 .. k-1 the
+        // sample survived (1 on a hit, 0 when it missed at step j+1)
+        const int reached = r.hit ? k : (int)r.depth;
+        label[o] = __fdiv_rn(__int2float_rn(reached - j - 1), __int2float_rn(k - j - 1));
         o++;
     }
 }

@@ -119,7 +119,8 @@ def test_training_rows_from_traces_exact():
             for j in range(2, k - 1):
                 if r["hit"] or r["depth"] > j:
                     want_f.append([O.flog2p1(int(deg[r["vert"][j]])), float(j), O.flog2p1(int(r["factor"][j + 1]))])
-                    want_l.append(float(r["hit"]))
+                    reached = k if r["hit"] else int(r["depth"])
+                    want_l.append(np.float32(reached - j - 1) / np.float32(k - j - 1))
         assert np.array_equal(feat.cpu().numpy(), np.array(want_f, dtype=np.float32).reshape(-1, 3))
         assert np.array_equal(label.cpu().numpy(), np.array(want_l, dtype=np.float32))
 
