@@ -133,7 +133,13 @@ typedef struct {
  * estimate, the NS cone, the GS prediction and its parts, the time per
  * sampler step, the triangle estimate, the selector features
  * (log2(t_gs / t_lo), log2(t_hi / t_lo), log2(n_s), each clamped to +-64) and
- * both decisions (1 = GS). */
+ * both decisions (1 = GS).  cost_model_gs is the rule the hybrid applies: GS
+ * iff t_gs < t_lo and GS's relative error can meet eps at all, i.e.
+ * z sqrt((1/P - 1) / (R C)) <= eps with P = c^-(k-1) (colours) or p^l
+ * (Bernoulli edges, l pattern edges), R samplers and C the pilot's estimate
+ * (the diagonal term of the Sec. 5.2 variance: no two matches covary
+ * negatively).  selector_gs is the head's own output; the hybrid follows it
+ * under the same error condition. */
 typedef struct {
     double n_s, t_lo, t_hi, t_gs, t_pre, t_search, c_step, triangles;
     float features[3];
@@ -241,7 +247,8 @@ gpm_status gpm_graph_info(const gpm_graph *g, uint64_t *n, uint64_t *m, uint64_t
  * GPM_GS: one colouring with cfg->colors colours, exact count on the
  * sparsified graph, scaled by c^(k-1) (eps and delta unused, ci = NaN).
  * GPM_HYBRID: a pilot NS round feeds the cost models of Sec. 4.3-4.4 and the
- * faster engine runs (Sec. 5.1, loose mode).  GPM_EXACT: exact count.
+ * faster engine runs (Sec. 5.1, loose mode); GS only when its error bound
+ * allows eps (see gpm_hybrid_info).  GPM_EXACT: exact count.
  * Returns GPM_ERR_NOT_CONVERGED (result filled) if n_max or max_seconds ends
  * the run first; for GPM_GS and GPM_EXACT, max_seconds bounds the exact
  * search on the device, and a search stopped by it leaves a lower bound in

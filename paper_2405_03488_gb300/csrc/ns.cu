@@ -821,10 +821,12 @@ namespace gpm {
 // by one neighbour costs the mean degree 2|E'|/|V|, an intersection of b
 // lists |V| p1 p2^(b-1) with p1 = 2|E'|/|V|^2 and p2 = T|V| / (2|E|^2) (the
 // substitution leaves p2 unchanged).  T comes from a short NS triangle pilot.
-// GS runs only if its prediction lies below the whole cone; otherwise NS
-// (the confidence-preserving choice).
+// GS runs only if its prediction lies below the whole cone and its error
+// bound (below) allows the target; otherwise NS (the confidence-preserving
+// choice).
 struct HybridModel {
     double n_s, t_lo, t_hi, t_gs, t_pre, t_search, c_step, triangles;
+    double gs_err_lb;   // lower bound on GS's relative error at 1 - delta
     int choose_gs;
 };
 
@@ -917,7 +919,20 @@ static gpm_status hybrid_model(gpm_graph *h, const Plan &p, double eps, double d
     hm->t_pre = bytes_pre / bw;
     hm->t_search = work * c_step;
     hm->t_gs = hm->t_pre + hm->t_search;
-    hm->choose_gs = hm->t_gs < hm->t_lo;
+    // GS can only be chosen when its own error can meet the target (Sec. 5.2,
+    // corrected): a match survives with probability P = c^-(k-1) (Bernoulli
+    // edges: p^l, l pattern edges) and no two matches covary negatively, so
+    // Var(C_hat) >= C (1/P - 1) and the relative error of R averaged samplers
+    // is at least z sqrt((1/P - 1) / (R C)), C from the pilot's mean
+    const double R = (cfg && cfg->samplers > 1) ? (double)cfg->samplers : 1.0;
+    double inv_p = std::pow(c, (double)(p.k - 1));
+    if (cfg && cfg->edge_p > 0.0) {
+        int l = 0;
+        for (int j = 0; j < p.k; j++) l += __builtin_popcount(p.back[j]);
+        inv_p = std::pow(1.0 / std::min(cfg->edge_p, 1.0), (double)l);
+    }
+    hm->gs_err_lb = (mu > 0.0) ? z * std::sqrt((inv_p - 1.0) / (R * mu)) : INFINITY;
+    hm->choose_gs = hm->gs_err_lb <= eps && hm->t_gs < hm->t_lo;
     return GPM_OK;
 }
 
@@ -949,7 +964,7 @@ static gpm_status hybrid_decide(gpm_graph *h, const Plan &p, double eps, double 
         info->cost_model_gs = hm->choose_gs;
         info->selector_gs = sel;
     }
-    if (sel >= 0) hm->choose_gs = sel;
+    if (sel >= 0) hm->choose_gs = sel && hm->gs_err_lb <= eps;
     return GPM_OK;
 }
 

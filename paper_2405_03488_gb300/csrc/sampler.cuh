@@ -38,7 +38,7 @@ constexpr uint32_t kLearnedMax = 256;   // larger candidate sets are drawn unifo
 #define GPM_REUSE_STREAM_BIAS 0
 #endif
 // a partner list longer than the on-chip buffer is staged window by window
-// (compact variant) instead of being searched in global memory
+// instead of being searched in global memory
 #ifndef GPM_PARTNER_WINDOWS
 #define GPM_PARTNER_WINDOWS 1
 #endif
@@ -539,9 +539,9 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 bool empty = dlen == 0;
                 int staged = -1;
                 uint32_t plen = 0;
-                // the partner's part above the bound; longer than the buffer, the
-                // compact variant stages it window by window (each window settles
-                // the driver entries up to its last element)
+                // the partner's part above the bound; longer than the buffer, it is
+                // staged window by window (each window settles the driver entries
+                // up to its last element)
                 const uint32_t *Q = nullptr;
                 uint32_t qn = 0;
                 bool windowed = false;
@@ -558,7 +558,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                         staged = partner;
                         plen = qn;
                         __syncwarp();
-                    } else if (kCompact && GPM_PARTNER_WINDOWS &&
+                    } else if (GPM_PARTNER_WINDOWS &&
                                (uint64_t)qn <= (uint64_t)GPM_WINDOW_RATIO * dlen) {
                         staged = partner;
                         windowed = true;
@@ -592,6 +592,8 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 // keeps the per-position form: its four inlined copies overlap the
                 // global non-edge searches, which the table form measured slower on
                 bool gpart = false;   // search the windowed partner in global memory
+                // every lane of the warp calls pred (the per-position form
+                // shuffles), so it comes first in any short-circuit condition
                 auto pred = [&](uint32_t y) -> bool {
                     bool ok = true;
                     if constexpr (kCompact) {
@@ -610,7 +612,8 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                             const bool edge = (back >> i) & 1u;
                             if (edge) {
                                 if (i == driver) continue;
-                                if (i == staged) ok = ok && lane_contains_shared(Sp, plen, y);
+                                if (i == staged)
+                                    ok = ok && (gpart ? lane_contains32(Q, qn, y) : lane_contains_shared(Sp, plen, y));
                                 else ok = ok && lane_contains32(Li, ni, y);
                             } else if (p.induced) {
                                 ok = ok && !lane_contains32(Li, ni, y);
@@ -652,7 +655,7 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                                 if (b >= dlen) break;
                                 const uint32_t yu = u == 0 ? y[0] : u == 1 ? y[1] : u == 2 ? y[2] : y[3];
                                 const bool in = (b + lane < dlen) && (tail || yu <= wlast);
-                                const bool ok = in && pred(yu);
+                                const bool ok = pred(yu) && in;
                                 const unsigned m = __ballot_sync(kFull, ok);
                                 if (ok) {
                                     const uint32_t pos = count + __popc(m & lanemask_lt());
@@ -674,25 +677,54 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                     }
                     gpart = windowed;
                     } else {
-                    for (uint32_t base = 0; base < dlen; base += 128) {
-                        uint32_t y[4];
-#pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            const uint32_t idx = base + 32 * u + lane;
-                            y[u] = idx < dlen ? __ldg(D + idx) : 0u;
+                    // four inlined copies of pred, same windows
+                    uint32_t pw = 0, dcur = 0;
+                    for (;;) {
+                        bool tail = true;
+                        uint32_t wlast = 0u;
+                        if (windowed) {
+                            const uint32_t wn = (qn - pw < a.cap) ? qn - pw : a.cap;
+                            __syncwarp();
+                            stage_list(Q + pw, wn, Sp);
+                            __syncwarp();
+                            plen = wn;
+                            pw += wn;
+                            tail = pw >= qn;
+                            wlast = Sp[wn - 1];
                         }
+                        bool stop = false;
+                        for (uint32_t base = dcur; base < dlen && !stop; base += 128) {
+                            uint32_t y[4];
 #pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            if (base + 32 * u >= dlen) break;
-                            const bool ok = pred(y[u]) && (base + 32 * u + lane < dlen);
-                            const unsigned m = __ballot_sync(kFull, ok);
-                            if (ok) {
-                                const uint32_t pos = count + __popc(m & lanemask_lt());
-                                if (pos < a.cap) Sc[pos] = y[u];
+                            for (int u = 0; u < 4; u++) {
+                                const uint32_t idx = base + 32 * u + lane;
+                                y[u] = idx < dlen ? __ldg(D + idx) : 0u;
                             }
-                            count += __popc(m);
+#pragma unroll
+                            for (int u = 0; u < 4; u++) {
+                                const uint32_t b = base + 32 * u;
+                                if (b >= dlen) break;
+                                const bool in = (b + lane < dlen) && (tail || y[u] <= wlast);
+                                const bool ok = pred(y[u]) && in;
+                                const unsigned m = __ballot_sync(kFull, ok);
+                                if (ok) {
+                                    const uint32_t pos = count + __popc(m & lanemask_lt());
+                                    if (pos < a.cap) Sc[pos] = y[u];
+                                }
+                                count += __popc(m);
+                                if (!tail) {
+                                    const unsigned im = __ballot_sync(kFull, in);
+                                    if (im != kFull) {
+                                        dcur = b + __popc(im);
+                                        stop = true;
+                                        break;
+                                    }
+                                }
+                            }
                         }
+                        if (tail || !stop) break;
                     }
+                    gpart = windowed;
                     }
                 }
                 if (!empty) {

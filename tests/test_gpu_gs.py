@@ -85,6 +85,22 @@ def test_hybrid_returns_a_consistent_engine_result():
     check_engine_result(r, og, "6-clique", 2)
 
 
+def test_hybrid_never_picks_gs_that_cannot_meet_the_target():
+    """A few planted cliques in a sparse graph: with c = 8 colours a 6-clique
+    survives with probability 8^-5, so GS's relative error is at least
+    z sqrt((8^5 - 1) / C), far above eps; the hybrid must run NS."""
+    rp, col = G.chung_lu(20000, n_cliques=20, clique_size=10, seed=5)
+    g = api.Graph(rp.cuda(), col.cuda())
+    C = g.exact_count("6-clique")
+    z = api.normal_quantile(1.0 - 0.01 / 2)
+    assert z * math.sqrt((8.0 ** 5 - 1.0) / C) > 0.05
+    info = g.hybrid_model("6-clique", eps=0.05, delta=0.01, seed=3, window=1 << 16, colors=8)
+    assert info["cost_model_gs"] == 0
+    r = g.estimate("6-clique", scheme=api.HYBRID, eps=0.05, delta=0.01, seed=3, window=1 << 16, n_max=1 << 22,
+                   colors=8)
+    assert r["scheme_used"] == api.NS
+
+
 def check_engine_result(r, og, name, colors):
     """Whichever engine the hybrid chose, its result is that engine's own: the
     oracle's online NS run (same seed and window) or its GS estimate."""
