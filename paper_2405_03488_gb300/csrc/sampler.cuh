@@ -448,7 +448,11 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
                 const uint32_t ds = above(d, DL, dn);
                 const uint32_t *S = DL + ds;
                 const uint32_t L = dn - ds;
-                const uint32_t q = ((int)lane < j && (int)lane != d) ? lane_find32(S, L, wm.v[lane]) : 0xFFFFFFFFu;
+                // a matched vertex at or below the bound cannot lie in the list's
+                // part above it: only the others are searched
+                const uint32_t q = ((int)lane < j && (int)lane != d && !(has_lo && wm.v[lane] <= lo))
+                                       ? lane_find32(S, L, wm.v[lane])
+                                       : 0xFFFFFFFFu;
                 count = L - (uint32_t)__popc(__ballot_sync(kFull, q != 0xFFFFFFFFu));
                 if (count) {
                     // smallest list index with t kept entries before it
