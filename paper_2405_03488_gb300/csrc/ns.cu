@@ -916,14 +916,8 @@ static gpm_status hybrid_model(gpm_graph *h, const Plan &p, double eps, double d
     }
     const double bytes_pre = 4.0 * 2.0 * E * 2.0 + 4.0 * 2.0 * E * pk + 8.0 * V * 3.0;
     const double bw = 2.0e12;   // effective sparsification bandwidth (B/s), measured on GB300
-    hm->t_pre = bytes_pre / bw;
-    hm->t_search = work * c_step;
-    hm->t_gs = hm->t_pre + hm->t_search;
-    // GS can only be chosen when its own error can meet the target (Sec. 5.2,
-    // corrected): a match survives with probability P = c^-(k-1) (Bernoulli
-    // edges: p^l, l pattern edges) and no two matches covary negatively, so
-    // Var(C_hat) >= C (1/P - 1) and the relative error of R averaged samplers
-    // is at least z sqrt((1/P - 1) / (R C)), C from the pilot's mean
+    // a match survives the sparsification with probability P = c^-(k-1)
+    // (Bernoulli edges: p^l, l pattern edges); R samplers are averaged
     const double R = (cfg && cfg->samplers > 1) ? (double)cfg->samplers : 1.0;
     double inv_p = std::pow(c, (double)(p.k - 1));
     if (cfg && cfg->edge_p > 0.0) {
@@ -931,6 +925,16 @@ static gpm_status hybrid_model(gpm_graph *h, const Plan &p, double eps, double d
         for (int j = 0; j < p.k; j++) l += __builtin_popcount(p.back[j]);
         inv_p = std::pow(1.0 / std::min(cfg->edge_p, 1.0), (double)l);
     }
+    hm->t_pre = bytes_pre / bw;
+    // the exact search visits every match of the sparsified graphs, R C P of
+    // them by the pilot's C, each at least one sampler step's work: a floor
+    // under the average-degree model, which a hub core makes far too low
+    hm->t_search = std::max(work * c_step, (mu > 0.0 ? R * mu / inv_p : 0.0) * c_step);
+    hm->t_gs = hm->t_pre + hm->t_search;
+    // GS can only be chosen when its own error can meet the target (Sec. 5.2,
+    // corrected): no two matches covary negatively, so Var(C_hat) >= C (1/P - 1)
+    // and the relative error of R averaged samplers is at least
+    // z sqrt((1/P - 1) / (R C)), C from the pilot's mean
     hm->gs_err_lb = (mu > 0.0) ? z * std::sqrt((inv_p - 1.0) / (R * mu)) : INFINITY;
     hm->choose_gs = hm->gs_err_lb <= eps && hm->t_gs < hm->t_lo;
     return GPM_OK;
