@@ -51,6 +51,16 @@ constexpr uint32_t kLearnedMax = 256;   // larger candidate sets are drawn unifo
 #endif
 // staging copies: cp.async, all of a list's copies in flight at once and no
 // register round trip (1), or four loads per lane then stores (0)
+// vertex-induced steps with one back-neighbour: counted and drawn from the
+// positions of the removed entries when the non-neighbour lists are short
+#ifndef GPM_INDUCED_POSITIONS
+#define GPM_INDUCED_POSITIONS 1
+#endif
+// ... used when the back-neighbour's list (above the bound) is this many times
+// longer than the non-neighbours' lists together
+#ifndef GPM_INDUCED_RATIO
+#define GPM_INDUCED_RATIO 2
+#endif
 #ifndef GPM_STAGE_ASYNC
 #define GPM_STAGE_ASYNC 1
 #endif
@@ -437,7 +447,102 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
             uint32_t count = 0;
             bool mat = true;
             const uint32_t back = p.back[j];
-            if ((MODE == MODE_INTERSECT_SINGLE || (MODE == MODE_LEARNED && j == k - 1)) && !p.induced &&
+            bool done = false;
+            // (batches with vertex-induced plans run the unrolled variant)
+            if constexpr (MODE == MODE_INTERSECT_SINGLE && !kCompact) {
+                if (GPM_INDUCED_POSITIONS && p.induced && (back & (back - 1)) == 0 &&
+                    !(p.reuse[j] >= 1 && prev_mat)) {
+                    // one back-neighbour v_d, vertex-induced: S_j is A = N(v_d) above
+                    // the bound without the entries that lie in a non-neighbour's
+                    // list or are matched vertices.  When the non-neighbours' lists
+                    // are short against A, each is walked once and the positions in A
+                    // of its entries (one ascending run per list, an entry counted in
+                    // the first list that holds it) give |S_j| and the drawn entry, as
+                    // in the edge-induced position form; A itself is never streamed.
+                    const int d = __ffs(back) - 1;
+                    const uint32_t *DL = row(d);
+                    const uint32_t dn = deg(d);
+                    const bool nnl = (int)lane < j && (int)lane != d;
+                    const uint32_t sumdeg = __reduce_add_sync(kFull, nnl ? (rn < (1u << 26) ? rn : (1u << 26)) : 0u);
+                    const uint32_t ds = above(d, DL, dn);
+                    const uint32_t *S = DL + ds;
+                    const uint32_t L = dn - ds;
+                    if (L >= 64 && (uint64_t)sumdeg * GPM_INDUCED_RATIO < (uint64_t)L) {
+                        const uint32_t amax = __ldg(S + L - 1);
+                        uint32_t nr = 0, run0 = 0, runn = 0;   // lane i: its run in Sc
+                        bool over = false;
+                        for (int i = 0; i < j && !over; i++) {
+                            if (i == d) continue;
+                            const uint32_t *B = row(i);
+                            const uint32_t bn = deg(i);
+                            const uint32_t bs = above(i, B, bn);
+                            const uint32_t start = nr;
+                            for (uint32_t base = bs; base < bn; base += 32) {
+                                const uint32_t idx = base + lane;
+                                const uint32_t y = idx < bn ? __ldg(B + idx) : 0xFFFFFFFFu;
+                                const bool in = idx < bn && y <= amax;
+                                uint32_t q = in ? lane_find32(S, L, y) : 0xFFFFFFFFu;
+                                for (int m = 0; m < j; m++) q = (y == wm.v[m]) ? 0xFFFFFFFFu : q;
+                                for (int i2 = 0; i2 < i; i2++) {
+                                    if (i2 == d) continue;
+                                    const uint32_t *B2 = row(i2);
+                                    const uint32_t n2 = deg(i2);
+                                    if (q != 0xFFFFFFFFu && lane_contains32(B2, n2, y)) q = 0xFFFFFFFFu;
+                                }
+                                const unsigned km = __ballot_sync(kFull, q != 0xFFFFFFFFu);
+                                const uint32_t pos = nr + __popc(km & lanemask_lt());
+                                if (q != 0xFFFFFFFFu && pos < a.cap) Sc[pos] = q;
+                                nr += __popc(km);
+                                if (nr > a.cap) {
+                                    over = true;
+                                    break;
+                                }
+                                // entries past A's last one cannot lie in A
+                                if (__ballot_sync(kFull, idx < bn && y > amax)) break;
+                            }
+                            if ((int)lane == i) {
+                                run0 = start;
+                                runn = nr - start;
+                            }
+                        }
+                        if (!over) {
+                            // matched vertices above the bound that lie in A (lane m);
+                            // the runs above leave them out
+                            uint32_t qm = 0xFFFFFFFFu;
+                            if (nnl && !(has_lo && wm.v[lane] <= lo)) qm = lane_find32(S, L, wm.v[lane]);
+                            __syncwarp();
+                            count = L - nr - (uint32_t)__popc(__ballot_sync(kFull, qm != 0xFFFFFFFFu));
+                            if (count) {
+                                // smallest position with t kept entries before it
+                                const uint32_t t = (uint32_t)index_map(r, count);
+                                uint32_t idx = t;
+                                for (;;) {
+                                    // removed positions <= idx: lane i counts its run
+                                    uint32_t c = 0;
+                                    if (nnl && runn) {
+                                        uint32_t lo2 = 0, hi2 = runn;
+                                        while (lo2 < hi2) {
+                                            const uint32_t mid = (lo2 + hi2) >> 1;
+                                            if (Sc[run0 + mid] <= idx) lo2 = mid + 1;
+                                            else hi2 = mid;
+                                        }
+                                        c = lo2;
+                                    }
+                                    c += (qm <= idx) ? 1u : 0u;
+                                    const uint32_t nx = t + __reduce_add_sync(kFull, c);
+                                    if (nx == idx) break;
+                                    idx = nx;
+                                }
+                                x = __ldg(S + idx);
+                            }
+                            mat = false;
+                            done = true;
+                        }
+                    }
+                }
+            }
+            if (done) {
+            } else if ((MODE == MODE_INTERSECT_SINGLE || (MODE == MODE_LEARNED && j == k - 1)) && !p.induced &&
                 (back & (back - 1)) == 0) {
                 // one back-neighbour v_d, edge-induced: S_j is N(v_d) above the
                 // bound without the matched vertices it holds, so |S_j| and its
@@ -876,10 +981,10 @@ __device__ SampleOut sample_one(const DGraph &g, const PlanT &p, const RunArgs &
     return out;
 }
 
-// True when some step of an edge-induced plan has one back-neighbour, the
-// steps the MODE_INTERSECT_SINGLE variant evaluates by list positions.
+// True when some step of the plan has one back-neighbour, the steps the
+// MODE_INTERSECT_SINGLE variant evaluates by list positions.
 inline bool plan_single_steps(const Plan &p) {
-    if (p.induced) return false;
+    if (p.induced && !GPM_INDUCED_POSITIONS) return false;
     for (int j = 2; j < p.k; j++)
         if ((p.back[j] & (p.back[j] - 1u)) == 0) return true;
     return false;

@@ -95,6 +95,22 @@ def test_sampled_list_searches_bit_exact(cap):
             assert_same_records(gpu, cpu, k)
 
 
+@pytest.mark.parametrize("cap", [32, 512])
+def test_induced_single_list_positions_bit_exact(cap):
+    """Vertex-induced steps with one back-neighbour on a skewed graph: the
+    back-neighbour's list is long (a hub) and the non-neighbours' lists short,
+    so the removed entries are located by their positions in it; more of them
+    than the buffer holds (cap 32) falls back to streaming the list."""
+    rp, col = G.rmat(14, 16, seed=9)
+    g, og = pair(rp, col)
+    for name in ("3-star", "4-path", "tailed-triangle", "4-cycle"):
+        k, edges = G.pattern(name)
+        gpu = g.trace((k, edges, True), seed=21, first=0, count=20000, cap=cap)
+        _, cpu = O.ns_run(og, O.plan(k, edges, True), seed=21, first=0, count=20000, trace=True)
+        assert_same_records(gpu, cpu, k)
+        assert gpu["hit"].sum() > 0
+
+
 def test_sums_match_oracle_er_triangle_1e6():
     """ER G(n=10^4, p=0.002), triangle, 10^6 samples, seed 1."""
     rp, col = G.erdos_renyi(10_000, 0.002, seed=1)
