@@ -15,17 +15,20 @@
 // The weight starts at M = m (oriented first edge) or 2m.
 //
 // Layout: the warp keeps the partial match, the per-step factors and two
-// candidate buffers of `cap` entries in shared memory; lane i holds the CSR
-// range of v_i.  S_j is built by streaming the shortest back-neighbour list
-// (coalesced 128-byte warp loads) and testing each element against the other
-// lists with per-lane binary searches, the next shortest list staged on chip
-// when its part above the bound fits `cap`, compacting survivors with ballots.
-// When S_j extends S_{j-1} by one more adjacency (cliques and similar), it is
-// built from S_{j-1} on chip and only N(v_{j-1}) is read.  A set larger than
-// `cap` is counted in one pass and its drawn element found in a second pass.
-// A step of an edge-induced pattern with a single back-neighbour (paths,
-// stars, cycles) never builds S_j: its size and drawn element follow from
-// positions in that neighbour's list (the MODE_INTERSECT_SINGLE variant).
+// candidate buffers of `cap` entries in shared memory; lane i holds the row
+// start, degree and first-upper-neighbour offset of v_i (offsets inside a
+// list are 32-bit).  S_j is built by streaming the shortest back-neighbour
+// list (coalesced 128-byte warp loads) and testing each element against the
+// other lists with per-lane binary searches, the next shortest list (its part
+// above the bound) copied on chip by cp.async, whole or, when longer than
+// `cap`, window by window, compacting survivors with ballots.  When S_j
+// extends S_{j-1} by one more adjacency (cliques and similar), it is built
+// from S_{j-1} on chip and only N(v_{j-1}) is read.  A set larger than `cap`
+// is counted in one pass and its drawn element found in a second pass.  A step
+// with a single back-neighbour (paths, stars, cycles) never builds S_j: its
+// size and drawn element follow from positions in that neighbour's list, of
+// the matched vertices (edge-induced) or also of the non-neighbours' entries
+// (vertex-induced) (the MODE_INTERSECT_SINGLE variant).
 //
 // CHECK mode draws x from the single list L_j = N(v_p) above the lower bound
 // (p the last back-neighbour), weighs |L_j|, and verifies the remaining
