@@ -7,7 +7,9 @@ first read b + n/2 < b + n, its last b < len); the warp's 32-ary upper bound
 reads a slot only below its open upper end, which never grows (the 32-bit form
 computes the piece length as ((hi - lo - 1) >> 5) + 1, the same ceiling).
 The windowed staging settles every driver entry exactly once, in order, and
-reads the partner only inside its list.  CPU only."""
+reads the partner only inside its list; the vertex-induced single-list step
+counts |S_j| and draws S_j's t-th entry from the positions of the removed
+entries alone.  CPU only."""
 import numpy as np
 import pytest
 
@@ -156,3 +158,60 @@ def test_windowed_partner_staging_settles_every_driver_entry_once(seed):
             assert got == sorted(set(D) & set(Q))
             assert all(0 <= r < qn for r in rq) and all(0 <= r < dlen for r in rd)
             assert len(set(rq)) == len(rq)     # every partner entry staged at most once
+
+
+def induced_positions_draw(A, nn_lists, matched, t):
+    """The vertex-induced single-list step, transcribed: the positions in A of
+    the entries of each non-neighbour list (one ascending run per list, an
+    entry counted in the first list holding it, matched vertices left out),
+    the positions of the matched vertices in A apart, |S| = |A| - removed, and
+    the drawn position by the fixed point idx = t + #(removed <= idx)."""
+    pos = {y: q for q, y in enumerate(A)}
+    amax = A[-1]
+    runs = []
+    for i, B in enumerate(nn_lists):
+        run = []
+        for y in B:
+            if y > amax:
+                break
+            q = pos.get(y)
+            if q is None or y in matched:
+                continue
+            if any(y in set(nn_lists[i2]) for i2 in range(i)):
+                continue
+            run.append(q)
+        assert run == sorted(run) and len(set(run)) == len(run)
+        runs.append(run)
+    qm = [pos[v] for v in matched if v in pos]
+    removed = sum(len(r) for r in runs) + len(qm)
+    count = len(A) - removed
+    if count == 0:
+        return count, None
+    assert 0 <= t < count
+    idx = t
+    while True:
+        c = sum(int(np.searchsorted(r, idx, side="right")) for r in runs) + sum(q <= idx for q in qm)
+        nx = t + c
+        if nx == idx:
+            break
+        idx = nx
+    assert 0 <= idx < len(A)
+    return count, idx
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_induced_single_list_positions_draw_the_right_entry(seed):
+    rng = np.random.default_rng(seed)
+    for trial in range(200):
+        universe = int(rng.integers(20, 400))
+        A = sorted(rng.choice(universe, size=int(rng.integers(1, universe // 2 + 1)), replace=False).tolist())
+        nn_lists = [sorted(rng.choice(universe + 50, size=int(rng.integers(0, 40)), replace=False).tolist())
+                    for _ in range(int(rng.integers(1, 4)))]
+        matched = set(rng.choice(universe, size=int(rng.integers(0, 4)), replace=False).tolist())
+        removed = set().union(*[set(b) for b in nn_lists]) | matched
+        S = [y for y in A if y not in removed]
+        for t in range(len(S)):
+            count, idx = induced_positions_draw(A, nn_lists, matched, t)
+            assert count == len(S) and A[idx] == S[t]
+        if not S:
+            assert induced_positions_draw(A, nn_lists, matched, 0) == (0, None)
